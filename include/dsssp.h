@@ -1,0 +1,176 @@
+/*
+ * dsssp.h -- C ABI of the GB300 delta-stepping single-source shortest-path library.
+ *
+ * The method is the delta-stepping algorithm of Meyer and Sanders as restated
+ * in linear-algebra form by Sridhar et al., "Delta-stepping SSSP: from Vertices
+ * and Edges to GraphBLAS Implementations" (IPDPSW 2019):
+ *   - Section III-A / Fig. 1: split every vertex's out-arcs into light
+ *     (weight <= Delta) and heavy (weight > Delta) sets, A_L and A_H;
+ *   - Section III-B: bucket B_i holds the vertices with i*Delta <= t < (i+1)*Delta;
+ *   - Section IV-C / Fig. 1 (left): the light relaxation of bucket i is the masked
+ *     min-plus product t_Req = A_L^T (t o t_Bi), repeated until no vertex
+ *     re-enters B_i; then one heavy pass t_Req = A_H^T (t o S) over the set S of
+ *     vertices processed in the bucket; then the next non-empty bucket.
+ *
+ * Conventions shared by every entry point:
+ *   - A graph is directed; CSR row v lists the out-arcs of v (Section II-A).
+ *     row_ptr has n+1 int64 entries, col has m int32 heads, weights are m int32
+ *     or m float32 values. Self-loops and repeated arcs are accepted.
+ *   - Weights must be non-negative and finite (NaN, +-inf and negative values
+ *     are rejected). A float32 -0.0 is stored as +0.0.
+ *   - Path sums use the weight type's own addition: float32 adds round to
+ *     nearest-even after every arc (an overflow to +inf reads as unreachable);
+ *     int32 adds are exact and saturate at INT32_MAX, which reads as unreachable.
+ *     Distances are the least fixed point of d[s] = 0, d[v] = min_(u,v) d[u] (+) w;
+ *     every relaxation order reaches the same bits.
+ *   - pred[v] is the smallest u with an arc (u,v) such that d[u] (+) w(u,v) == d[v];
+ *     pred[src] = src; unreached vertices get dist = +inf (float32) or
+ *     INT32_MAX (int32) and pred = -1.
+ *   - Every pointer to vertex or arc data is a DEVICE pointer of the current
+ *     CUDA device unless the argument says otherwise. `stream` is a
+ *     cudaStream_t passed as void*; NULL means the legacy default stream.
+ *     All device work is ordered on that stream.
+ *   - Functions return a dsssp_status and never abort the process. Device-side
+ *     failures (a timed-out wait, a phase cap) are reported as status codes,
+ *     never as a trap.
+ *   - Limits: 1 <= n <= 2^31 - 2 and m <= 2^31 - 1.
+ */
+#ifndef DSSSP_H
+#define DSSSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DSSSP_OK = 0,
+    DSSSP_ERR_INVALID_ARG = 1,   /* a scalar argument is out of range or a pointer is NULL      */
+    DSSSP_ERR_BAD_GRAPH = 2,     /* row_ptr not monotone / not starting at 0, head out of range  */
+    DSSSP_ERR_NEG_WEIGHT = 3,    /* a weight is negative, NaN or infinite                        */
+    DSSSP_ERR_NOT_CONVERGED = 4, /* the phase cap of dsssp_options.max_phases was reached       */
+    DSSSP_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out (dsssp_options.timeout_ns) */
+    DSSSP_ERR_CUDA = 6,          /* a CUDA runtime call failed                                   */
+    DSSSP_ERR_NO_TAPE = 7,       /* reserved                                                     */
+    DSSSP_ERR_OOM = 8,           /* a device allocation failed                                   */
+    DSSSP_ERR_UNSUPPORTED = 9    /* the device or launch shape cannot run this entry point      */
+} dsssp_status;
+
+typedef enum { DSSSP_I32 = 0, DSSSP_F32 = 1 } dsssp_dtype;
+
+/* Opaque graph handle: a device copy of the CSR plus the per-Delta light/heavy
+ * layouts and the solver workspace. Owned by the library. */
+typedef struct dsssp_graph dsssp_graph;
+
+/* Solver execution schemes (dsssp_options.mode). */
+typedef enum {
+    DSSSP_MODE_PERSISTENT = 0,   /* one cooperative kernel runs every phase; grid-wide barriers  */
+    DSSSP_MODE_STEPPED = 1       /* one kernel launch per phase, loop driven by the host          */
+} dsssp_mode;
+
+/* dsssp_options.flags */
+#define DSSSP_FLAG_ASYNC 0x1u    /* do not wait for the solve: device-side status is kept in the
+                                    graph and returned by dsssp_graph_sync()                        */
+
+/* Test hooks (dsssp_options.test_hook): exercise error paths without a fault. */
+#define DSSSP_HOOK_NONE 0
+#define DSSSP_HOOK_STALL_BARRIER 1  /* block 1 leaves the persistent kernel before its first
+                                       barrier, so the others' bounded wait runs out and the
+                                       solve returns DSSSP_ERR_TIMEOUT                           */
+
+typedef struct {
+    uint32_t struct_size;   /* sizeof(dsssp_options); 0 fields mean "default"                  */
+    uint32_t flags;         /* DSSSP_FLAG_*                                                      */
+    int32_t  mode;          /* dsssp_mode; default DSSSP_MODE_PERSISTENT                        */
+    int32_t  block_size;    /* threads per block, multiple of 32, <= 512; default 512           */
+    int32_t  grid_size;     /* blocks of the persistent kernel; default = all co-resident blocks */
+    int32_t  big_degree;    /* arc segments longer than this are spread over the whole grid;
+                               default 512                                                        */
+    int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
+    int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
+    int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
+    int32_t  reserved[5];
+} dsssp_options;
+
+/* Counters of one solve (filled when a non-NULL pointer is passed; this makes
+ * the call wait for the solve). Times are device-side (%globaltimer), per phase kind. */
+typedef struct {
+    int64_t buckets;          /* non-empty buckets processed                                   */
+    int64_t light_phases;     /* light relaxation rounds (inner loop of Fig. 1)                */
+    int64_t heavy_phases;     /* heavy passes                                                   */
+    int64_t big_phases;       /* grid-wide passes over long arc segments                       */
+    int64_t select_phases;    /* next-bucket searches (far-pile compactions)                   */
+    int64_t vertices_light;   /* sum of |frontier| over light rounds                           */
+    int64_t vertices_heavy;   /* sum of |S| over heavy passes                                   */
+    int64_t arcs_light;       /* light arcs relaxed                                             */
+    int64_t arcs_heavy;       /* heavy arcs relaxed                                             */
+    int64_t far_scanned;      /* far-pile entries examined by next-bucket searches             */
+    int64_t improvements;     /* strict distance decreases                                      */
+    int64_t ns_light;         /* device time in light rounds (incl. their long-segment passes) */
+    int64_t ns_heavy;         /* device time in heavy passes                                    */
+    int64_t ns_select;        /* device time in next-bucket searches                           */
+    int64_t ns_total;         /* device time of the whole solve kernel                          */
+    int64_t grid_size;        /* blocks used                                                    */
+    int64_t block_size;       /* threads per block used                                          */
+    int64_t reserved[7];
+} dsssp_stats;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *dsssp_status_string(dsssp_status s);
+
+/* Fill *opt with the defaults above. */
+dsssp_status dsssp_options_default(dsssp_options *opt);
+
+/* Create a graph handle: validates and copies the CSR to the current device.
+ * Section II-A (adjacency matrix, row = out-arcs), Section III-A (weights).
+ *   n, m        vertex and arc counts (limits in the file header);
+ *   row_ptr     int64[n+1], col int32[m], w int32[m] or float32[m];
+ *   dtype       DSSSP_I32 or DSSSP_F32;
+ *   device_ptrs 1: row_ptr/col/w are device pointers; 0: host pointers;
+ *   stream      ordering stream for the copies and validation;
+ *   out         receives the handle (owned by the library until dsssp_graph_destroy).
+ * The caller's buffers are not retained. Waits for validation to finish.
+ * Errors: INVALID_ARG, BAD_GRAPH, NEG_WEIGHT, OOM, CUDA. */
+dsssp_status dsssp_graph_create(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                                const void *w, dsssp_dtype dtype, int device_ptrs, void *stream,
+                                dsssp_graph **out);
+
+/* Release a handle and all device memory it owns (waits for its pending work). */
+dsssp_status dsssp_graph_destroy(dsssp_graph *g);
+
+/* Query a handle: any output pointer may be NULL. */
+dsssp_status dsssp_graph_info(const dsssp_graph *g, int64_t *n, int64_t *m, int32_t *dtype);
+
+/* Light/heavy split for one Delta (Section III-A, Section IV-A, Fig. 1:
+ * A_L = A o (A <= Delta), A_H = A o (A > Delta)). Builds, on `stream`, a copy
+ * of the arcs in which every row lists its light arcs first, then its heavy
+ * arcs, each group in input order; caches it in the handle (a few Deltas are
+ * kept, least recently used evicted). dsssp_solve calls this itself when
+ * needed; calling it first lets the split be timed on its own.
+ * delta > 0, may be +inf (every arc light). Errors: INVALID_ARG, OOM, CUDA. */
+dsssp_status dsssp_prepare(dsssp_graph *g, double delta, void *stream);
+
+/* One delta-stepping solve (Fig. 1; Section III-C, IV-C, IV-D):
+ *   src    source vertex, 0 <= src < n;
+ *   delta  bucket width, > 0 (may be +inf);
+ *   dist   device int32[n] or float32[n] (the graph's dtype), written on success;
+ *   pred   device int32[n], written on success (may be NULL);
+ *   opt    NULL for defaults;
+ *   stats  NULL, or host struct filled after the solve (then the call waits);
+ * Unless DSSSP_FLAG_ASYNC is set the call waits for the solve and returns its
+ * device-side status. Solves on one handle share its workspace: issue them on
+ * one stream (or serialize them). Errors: INVALID_ARG, TIMEOUT, NOT_CONVERGED,
+ * OOM, CUDA, UNSUPPORTED. */
+dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, int32_t *pred,
+                         const dsssp_options *opt, dsssp_stats *stats, void *stream);
+
+/* Wait for the handle's outstanding work on `stream` and return (and clear)
+ * the first device-side status recorded by asynchronous solves. */
+dsssp_status dsssp_graph_sync(dsssp_graph *g, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DSSSP_H */

@@ -1,0 +1,410 @@
+// api.cu -- host side of the C ABI declared in include/dsssp.h: graph handles,
+// the per-Delta split cache, the solver workspace and launch orchestration.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "dsssp_internal.cuh"
+
+using namespace dsssp;
+
+namespace {
+
+constexpr int kSplitCache = 4;
+
+struct Split {
+    double delta = 0.0;
+    bool valid = false;
+    uint64_t last_use = 0;
+    uint2 *arcs = nullptr;      // m
+    uint4 *vinfo = nullptr;     // n
+    uint32_t *perm = nullptr;   // m: split position -> input arc index
+};
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+            changed = cudaSetDevice(dev) == cudaSuccess;
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct dsssp_graph {
+    int64_t n = 0, m = 0;
+    int dtype = 0;
+    int device = 0;
+    int sm_count = 0;
+    uint32_t *off = nullptr;      // n+1
+    int32_t *col = nullptr;       // m
+    uint32_t *wbits = nullptr;    // m
+    Split splits[kSplitCache];
+    uint64_t use_clock = 0;
+    // solver workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    SolveArgs args{};
+    Ctl *ctl = nullptr;           // device
+    Ctl *ctl_host = nullptr;      // pinned host mirror
+    int32_t *sticky = nullptr;    // device: first error of asynchronous solves
+    int occ_block = 0, occ_blocks_per_sm = 0;
+};
+
+namespace {
+
+dsssp_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DSSSP_OK;
+    if (e == cudaErrorMemoryAllocation) return DSSSP_ERR_OOM;
+    if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) return DSSSP_ERR_UNSUPPORTED;
+    return DSSSP_ERR_CUDA;
+}
+
+#define DSSSP_TRY(expr)                                      \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) {                             \
+            cudaGetLastError();                              \
+            return cuda_status(_e);                          \
+        }                                                    \
+    } while (0)
+
+__global__ void k_sticky(const Ctl *c, int32_t *sticky) {
+    int e = *(const volatile int *)&c->err;
+    if (e != 0) atomicCAS(sticky, 0, e);
+}
+
+void free_split(Split &s) {
+    cudaFree(s.arcs);
+    cudaFree(s.vinfo);
+    cudaFree(s.perm);
+    s = Split{};
+}
+
+dsssp_status ensure_split(dsssp_graph *g, double delta, cudaStream_t st, Split **out) {
+    g->use_clock++;
+    for (auto &s : g->splits) {
+        if (s.valid && (s.delta == delta || (std::isinf(s.delta) && std::isinf(delta)))) {
+            s.last_use = g->use_clock;
+            *out = &s;
+            return DSSSP_OK;
+        }
+    }
+    Split *slot = &g->splits[0];
+    for (auto &s : g->splits) {
+        if (!s.valid) { slot = &s; break; }
+        if (s.last_use < slot->last_use) slot = &s;
+    }
+    if (slot->valid) {
+        DSSSP_TRY(cudaStreamSynchronize(st));
+        free_split(*slot);
+    }
+    const size_t m = (size_t)g->m, n = (size_t)g->n;
+    DSSSP_TRY(cudaMalloc(&slot->arcs, (m ? m : 1) * sizeof(uint2)));
+    DSSSP_TRY(cudaMalloc(&slot->vinfo, n * sizeof(uint4)));
+    DSSSP_TRY(cudaMalloc(&slot->perm, (m ? m : 1) * sizeof(uint32_t)));
+    uint32_t *pl = nullptr, *tiles = nullptr;
+    DSSSP_TRY(cudaMallocAsync(&pl, (m + 1) * sizeof(uint32_t), st));
+    DSSSP_TRY(cudaMallocAsync(&tiles, split_scratch_tiles((int64_t)m) * sizeof(uint32_t), st));
+    const uint32_t lmax = light_max_key(g->dtype, delta);
+    cudaError_t e = launch_split(g->n, g->m, g->off, g->col, g->wbits, lmax, pl, tiles, slot->arcs,
+                                 slot->vinfo, slot->perm, st);
+    cudaFreeAsync(pl, st);
+    cudaFreeAsync(tiles, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_split(*slot);
+        return cuda_status(e);
+    }
+    slot->delta = delta;
+    slot->valid = true;
+    slot->last_use = g->use_clock;
+    *out = slot;
+    return DSSSP_OK;
+}
+
+dsssp_status ensure_workspace(dsssp_graph *g) {
+    if (g->ws) return DSSSP_OK;
+    const size_t n = (size_t)g->n;
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    size_t bytes = 0;
+    const size_t o_packed = bytes; bytes += up(n * 8);
+    const size_t o_near = bytes;   bytes += up(n * 4);
+    const size_t o_far = bytes;    bytes += up(n * 4);
+    const size_t o_s = bytes;      bytes += up(n * 4);
+    const size_t o_f0 = bytes;     bytes += up(n * 4);
+    const size_t o_f1 = bytes;     bytes += up(n * 4);
+    const size_t o_S = bytes;      bytes += up(n * 4);
+    const size_t o_far0 = bytes;   bytes += up(n * 4);
+    const size_t o_far1 = bytes;   bytes += up(n * 4);
+    const size_t o_big = bytes;    bytes += up(n * 16);
+    const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
+    const size_t o_sticky = bytes; bytes += up(sizeof(int32_t));
+    char *base = nullptr;
+    DSSSP_TRY(cudaMalloc(&base, bytes));
+    DSSSP_TRY(cudaMemset(base + o_ctl, 0, sizeof(Ctl)));
+    DSSSP_TRY(cudaMemset(base + o_sticky, 0, sizeof(int32_t)));
+    g->ws = base;
+    g->ws_bytes = bytes;
+    SolveArgs &a = g->args;
+    a.packed = (unsigned long long *)(base + o_packed);
+    a.near_stamp = (uint32_t *)(base + o_near);
+    a.far_flag = (uint32_t *)(base + o_far);
+    a.s_stamp = (uint32_t *)(base + o_s);
+    a.F0 = (uint32_t *)(base + o_f0);
+    a.F1 = (uint32_t *)(base + o_f1);
+    a.S = (uint32_t *)(base + o_S);
+    a.FAR0 = (uint32_t *)(base + o_far0);
+    a.FAR1 = (uint32_t *)(base + o_far1);
+    a.BIG = (uint4 *)(base + o_big);
+    a.ctl = (Ctl *)(base + o_ctl);
+    g->ctl = a.ctl;
+    g->sticky = (int32_t *)(base + o_sticky);
+    return DSSSP_OK;
+}
+
+void fill_stats(const Ctl &c, int grid, int block, dsssp_stats *s) {
+    std::memset(s, 0, sizeof *s);
+    s->buckets = c.st[ST_BUCKETS];
+    s->light_phases = c.st[ST_LIGHT];
+    s->heavy_phases = c.st[ST_HEAVY];
+    s->big_phases = c.st[ST_BIGP];
+    s->select_phases = c.st[ST_SELECT];
+    s->vertices_light = c.st[ST_VLIGHT];
+    s->vertices_heavy = c.st[ST_VHEAVY];
+    s->arcs_light = c.st[ST_ALIGHT];
+    s->arcs_heavy = c.st[ST_AHEAVY];
+    s->far_scanned = c.st[ST_FARSCAN];
+    s->improvements = c.st[ST_IMPROVE];
+    s->ns_light = c.st[ST_NSLIGHT];
+    s->ns_heavy = c.st[ST_NSHEAVY];
+    s->ns_select = c.st[ST_NSSELECT];
+    s->ns_total = c.st[ST_NSTOTAL];
+    s->grid_size = grid;
+    s->block_size = block;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dsssp_status_string(dsssp_status s) {
+    switch (s) {
+    case DSSSP_OK: return "ok";
+    case DSSSP_ERR_INVALID_ARG: return "invalid argument";
+    case DSSSP_ERR_BAD_GRAPH: return "malformed CSR graph";
+    case DSSSP_ERR_NEG_WEIGHT: return "negative, NaN or infinite weight";
+    case DSSSP_ERR_NOT_CONVERGED: return "phase cap reached before convergence";
+    case DSSSP_ERR_TIMEOUT: return "bounded device-side wait timed out";
+    case DSSSP_ERR_CUDA: return "CUDA runtime error";
+    case DSSSP_ERR_NO_TAPE: return "no tape";
+    case DSSSP_ERR_OOM: return "out of device memory";
+    case DSSSP_ERR_UNSUPPORTED: return "unsupported device or launch shape";
+    }
+    return "unknown status";
+}
+
+dsssp_status dsssp_options_default(dsssp_options *opt) {
+    if (!opt) return DSSSP_ERR_INVALID_ARG;
+    std::memset(opt, 0, sizeof *opt);
+    opt->struct_size = sizeof *opt;
+    opt->mode = DSSSP_MODE_PERSISTENT;
+    opt->block_size = 512;
+    opt->grid_size = 0;
+    opt->big_degree = 512;
+    opt->max_phases = (int64_t)1 << 26;
+    opt->timeout_ns = 2000000000LL;
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_graph_create(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                                const void *w, dsssp_dtype dtype, int device_ptrs, void *stream,
+                                dsssp_graph **out) {
+    if (!out) return DSSSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || n > ((int64_t)1 << 31) - 2 || m < 0 || m > ((int64_t)1 << 31) - 1) return DSSSP_ERR_INVALID_ARG;
+    if (!row_ptr || (m > 0 && (!col || !w))) return DSSSP_ERR_INVALID_ARG;
+    if (dtype != DSSSP_I32 && dtype != DSSSP_F32) return DSSSP_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    dsssp_graph *g = new (std::nothrow) dsssp_graph();
+    if (!g) return DSSSP_ERR_OOM;
+    g->n = n;
+    g->m = m;
+    g->dtype = dtype;
+    auto fail = [&](dsssp_status s) {
+        dsssp_graph_destroy(g);
+        return s;
+    };
+    if (cudaGetDevice(&g->device) != cudaSuccess) return fail(DSSSP_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess)
+        return fail(DSSSP_ERR_CUDA);
+    const size_t mm = m ? (size_t)m : 1;
+    int64_t *rp_dev = nullptr;
+    int32_t *col_tmp = nullptr;
+    int *flags = nullptr;
+    cudaError_t e = cudaSuccess;
+    if ((e = cudaMalloc(&g->off, (size_t)(n + 1) * sizeof(uint32_t))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMalloc(&g->col, mm * sizeof(int32_t))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMalloc(&g->wbits, mm * sizeof(uint32_t))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMallocHost(&g->ctl_host, sizeof(Ctl))) != cudaSuccess) return fail(cuda_status(e));
+    if ((e = cudaMallocAsync(&flags, sizeof(int), st)) != cudaSuccess) return fail(cuda_status(e));
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (device_ptrs) {
+        rp_dev = const_cast<int64_t *>(row_ptr);
+    } else {
+        if ((e = cudaMallocAsync(&rp_dev, (size_t)(n + 1) * sizeof(int64_t), st)) != cudaSuccess) return fail(cuda_status(e));
+        e = cudaMemcpyAsync(rp_dev, row_ptr, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    }
+    (void)col_tmp;
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->col, col, (size_t)m * sizeof(int32_t), kind, st);
+    if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->wbits, w, (size_t)m * sizeof(uint32_t), kind, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_validate(n, m, rp_dev, g->col, g->wbits, dtype, g->off, flags, st);
+    int hflags = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflags, flags, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (!device_ptrs && rp_dev) cudaFreeAsync(rp_dev, st);
+    cudaFreeAsync(flags, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(cuda_status(e));
+    }
+    if (hflags & 1) return fail(DSSSP_ERR_BAD_GRAPH);
+    if (hflags & 2) return fail(DSSSP_ERR_NEG_WEIGHT);
+    *out = g;
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_graph_destroy(dsssp_graph *g) {
+    if (!g) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaDeviceSynchronize();
+    for (auto &s : g->splits) free_split(s);
+    cudaFree(g->off);
+    cudaFree(g->col);
+    cudaFree(g->wbits);
+    cudaFree(g->ws);
+    if (g->ctl_host) cudaFreeHost(g->ctl_host);
+    delete g;
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_graph_info(const dsssp_graph *g, int64_t *n, int64_t *m, int32_t *dtype) {
+    if (!g) return DSSSP_ERR_INVALID_ARG;
+    if (n) *n = g->n;
+    if (m) *m = g->m;
+    if (dtype) *dtype = g->dtype;
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_prepare(dsssp_graph *g, double delta, void *stream) {
+    if (!g || !(delta > 0.0)) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    Split *s = nullptr;
+    return ensure_split(g, delta, (cudaStream_t)stream, &s);
+}
+
+dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, int32_t *pred,
+                         const dsssp_options *opt_in, dsssp_stats *stats, void *stream) {
+    if (!g || !dist || src < 0 || (int64_t)src >= g->n || !(delta > 0.0)) return DSSSP_ERR_INVALID_ARG;
+    dsssp_options opt;
+    dsssp_options_default(&opt);
+    if (opt_in) {
+        if (opt_in->struct_size != sizeof(dsssp_options)) return DSSSP_ERR_INVALID_ARG;
+        opt.flags = opt_in->flags;
+        opt.mode = opt_in->mode;
+        if (opt_in->block_size) opt.block_size = opt_in->block_size;
+        if (opt_in->grid_size) opt.grid_size = opt_in->grid_size;
+        if (opt_in->big_degree) opt.big_degree = opt_in->big_degree;
+        if (opt_in->max_phases) opt.max_phases = opt_in->max_phases;
+        if (opt_in->timeout_ns) opt.timeout_ns = opt_in->timeout_ns;
+        opt.test_hook = opt_in->test_hook;
+    }
+    if (opt.block_size < 32 || opt.block_size > 512 || opt.block_size % 32 != 0) return DSSSP_ERR_INVALID_ARG;
+    if (opt.big_degree < 32 || opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
+    if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    Split *sp = nullptr;
+    dsssp_status rc = ensure_split(g, delta, st, &sp);
+    if (rc != DSSSP_OK) return rc;
+    if ((rc = ensure_workspace(g)) != DSSSP_OK) return rc;
+
+    // grid: all co-resident blocks (the persistent kernel waits on every block)
+    if (g->occ_block != opt.block_size) {
+        int bps = 0;
+        DSSSP_TRY(solve_occupancy(opt.block_size, &bps));
+        g->occ_block = opt.block_size;
+        g->occ_blocks_per_sm = bps;
+    }
+    const int max_grid = g->occ_blocks_per_sm * g->sm_count;
+    if (max_grid < 1) return DSSSP_ERR_UNSUPPORTED;
+    int grid = opt.grid_size ? opt.grid_size : max_grid;
+    if (opt.mode == DSSSP_MODE_PERSISTENT && grid > max_grid) return DSSSP_ERR_UNSUPPORTED;
+    if (opt.test_hook == DSSSP_HOOK_STALL_BARRIER && grid < 2) return DSSSP_ERR_INVALID_ARG;
+
+    SolveArgs a = g->args;
+    a.vinfo = sp->vinfo;
+    a.arcs = sp->arcs;
+    a.delta = delta;
+    a.timeout_ns = opt.timeout_ns;
+    a.max_phases = opt.max_phases;
+    a.n = (uint32_t)g->n;
+    a.src = (uint32_t)src;
+    a.inf_key = key_inf(g->dtype);
+    a.big_degree = (uint32_t)opt.big_degree;
+    a.dtype = g->dtype;
+    a.test_hook = opt.test_hook;
+    a.nblocks = (uint32_t)grid;
+
+    DSSSP_TRY(launch_init(a, st));
+    if (opt.mode == DSSSP_MODE_PERSISTENT) {
+        DSSSP_TRY(launch_solve_persistent(a, grid, opt.block_size, st));
+    } else {
+        // host-driven loop: one kernel per phase, the serial step as a 1-thread kernel
+        for (int64_t ph = 0;; ++ph) {
+            DSSSP_TRY(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+            DSSSP_TRY(cudaStreamSynchronize(st));
+            const uint32_t mode = g->ctl_host->mode;
+            if (mode == MODE_DONE || g->ctl_host->err != 0) break;
+            DSSSP_TRY(launch_phase_stepped(a, mode, grid, opt.block_size, st));
+            DSSSP_TRY(launch_serial_step(a, st));
+        }
+    }
+    DSSSP_TRY(launch_unpack(a, dist, pred, st));
+    k_sticky<<<1, 1, 0, st>>>(g->ctl, g->sticky);
+    DSSSP_TRY(cudaGetLastError());
+    if ((opt.flags & DSSSP_FLAG_ASYNC) && !stats) return DSSSP_OK;
+    DSSSP_TRY(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+    DSSSP_TRY(cudaStreamSynchronize(st));
+    if (stats) fill_stats(*g->ctl_host, grid, opt.block_size, stats);
+    const int err = g->ctl_host->err;
+    if (err != 0) {
+        cudaMemsetAsync(g->sticky, 0, sizeof(int32_t), st);
+        return (dsssp_status)err;
+    }
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_graph_sync(dsssp_graph *g, void *stream) {
+    if (!g) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!g->sticky) {
+        DSSSP_TRY(cudaStreamSynchronize(st));
+        return DSSSP_OK;
+    }
+    int32_t h = 0;
+    DSSSP_TRY(cudaMemcpyAsync(&h, g->sticky, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    DSSSP_TRY(cudaMemsetAsync(g->sticky, 0, sizeof(int32_t), st));
+    DSSSP_TRY(cudaStreamSynchronize(st));
+    return (dsssp_status)h;
+}
+
+}  // extern "C"

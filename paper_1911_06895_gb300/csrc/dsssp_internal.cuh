@@ -1,0 +1,189 @@
+// dsssp_internal.cuh -- device-side state and helpers shared by the library's
+// kernels (split, solve) and its host API. Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dsssp.h"
+
+namespace dsssp {
+
+// ----------------------------------------------------------------------------
+// Keys. A tentative distance is kept as a 32-bit key whose unsigned order is
+// the order of the distances: the IEEE bits of a non-negative float32, or the
+// value of a non-negative int32. The paper's t vector (Fig. 1) is stored as
+// packed[v] = key(t[v]) << 32 | pred[v], so one 64-bit atomicMin updates the
+// distance and keeps the smallest predecessor among equal distances.
+constexpr uint32_t KEY_INF_F32 = 0x7F800000u;   // +inf
+constexpr uint32_t KEY_INF_I32 = 0x7FFFFFFFu;   // INT32_MAX
+constexpr uint32_t NO_PRED = 0xFFFFFFFFu;
+
+__host__ __device__ inline uint32_t key_inf(int dtype) {
+    return dtype == DSSSP_F32 ? KEY_INF_F32 : KEY_INF_I32;
+}
+
+// Exact value of a key as a double.
+__host__ __device__ inline double key_value(uint32_t k, int dtype) {
+    if (dtype == DSSSP_F32) {
+        union { uint32_t u; float f; } c;
+        c.u = k;
+        return (double)c.f;
+    }
+    return (double)k;
+}
+
+// bucket(x) = floor(x / Delta) (Section III-B), evaluated exactly: the double
+// quotient is correctly rounded, hence at most one above the true floor; an
+// exact fma() sign test corrects it.
+__host__ __device__ inline int64_t bucket_of_key(uint32_t k, int dtype, double delta) {
+    if (delta == (double)INFINITY) return 0;
+    double x = key_value(k, dtype);
+    double q = floor(x / delta);
+    if (q >= 9007199254740992.0) return q >= 9.2e18 ? INT64_MAX : (int64_t)q;
+    if (q > 0.0 && fma(q, delta, -x) > 0.0) q -= 1.0;
+    else if (fma(q + 1.0, delta, -x) <= 0.0) q += 1.0;
+    return (int64_t)q;
+}
+
+// Smallest key whose value is >= j * Delta exactly (the lower edge of bucket j);
+// key_inf when no finite value qualifies. "key < bucket_floor_key(i+1)" is
+// then exactly "bucket(key) <= i".
+__host__ __device__ inline uint32_t bucket_floor_key(int64_t j, int dtype, double delta) {
+    const uint32_t inf = key_inf(dtype);
+    if (delta == (double)INFINITY) return j <= 0 ? 0u : inf;
+    if (j <= 0) return 0u;
+    const double jd = (double)j;
+    const double p = jd * delta;                       // rounded; corrected below
+    const double maxv = key_value(inf - 1u, dtype);
+    if (!(p <= maxv * 1.0000001)) return inf;
+    uint32_t k;
+    if (dtype == DSSSP_F32) {
+        float f = (float)p;                            // nearest; corrected below
+        union { float f; uint32_t u; } c;
+        c.f = f;
+        k = c.u;
+        if (k > inf) k = inf;
+    } else {
+        double cp = ceil(p);
+        k = cp >= (double)inf ? inf : (uint32_t)cp;
+    }
+    // step down while the previous key still reaches j*Delta, up while k falls short
+    for (int it = 0; it < 4 && k > 0u && fma(jd, delta, -key_value(k - 1u, dtype)) <= 0.0; ++it) --k;
+    for (int it = 0; it < 4 && k < inf && fma(jd, delta, -key_value(k, dtype)) > 0.0; ++it) ++k;
+    return k;
+}
+
+// Largest weight key that is light (value <= Delta), Section III-A; light arcs
+// are exactly those with key <= light_max_key. Zero is light.
+__host__ __device__ inline uint32_t light_max_key(int dtype, double delta) {
+    const uint32_t inf = key_inf(dtype);
+    if (!(delta < key_value(inf - 1u, dtype))) return inf;   // every finite weight is light
+    // smallest key above Delta, minus one
+    uint32_t k;
+    if (dtype == DSSSP_F32) {
+        union { float f; uint32_t u; } c;
+        c.f = (float)delta;
+        k = c.u;
+    } else {
+        k = (uint32_t)floor(delta);
+    }
+    while (k > 0u && key_value(k, dtype) > delta) --k;
+    while (k + 1u < inf && key_value(k + 1u, dtype) <= delta) ++k;
+    if (key_value(k, dtype) > delta) return 0xFFFFFFFFu;      // nothing is light (delta < 0)
+    return k;
+}
+
+// ----------------------------------------------------------------------------
+// Solver phases. Each phase is one grid-wide step separated by a barrier.
+enum Mode : uint32_t {
+    MODE_LIGHT = 0,    // relax light arcs of the frontier F  (t_Req = A_L^T (t o t_Bi))
+    MODE_BIG = 1,      // relax long arc segments found in the previous phase, grid-wide
+    MODE_HEAVY = 2,    // relax heavy arcs of S               (t_Req = A_H^T (t o S))
+    MODE_SELECT = 3,   // next non-empty bucket: compact the far pile into F
+    MODE_DONE = 4
+};
+
+// Control block in device memory. The phase descriptor is written only by the
+// serial step of a barrier (one thread) and read by every block after it.
+struct Ctl {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    // phase descriptor
+    uint32_t mode;
+    uint32_t big_kind;      // 0: light segments, 1: heavy segments
+    uint32_t cur;           // frontier list being read (0/1); pushes go to cur^1
+    uint32_t far_cur;       // far list being read (0/1)
+    uint32_t qstamp;        // stamp of pushes into the next frontier
+    uint32_t sround;        // stamp of membership in S
+    uint32_t T;             // key < T  <=>  bucket <= i
+    uint32_t pad0;
+    int64_t bucket;         // current bucket index i
+    // list lengths (atomics)
+    uint32_t nF[2];
+    uint32_t nS;
+    uint32_t nFar[2];
+    uint32_t far_min;       // lower bound on the keys of live far-pile entries
+    uint32_t pad1[2];
+    unsigned long long big_ctr;   // (entries << 32) | arcs of the long-segment list
+    int32_t err;            // first dsssp_status != OK
+    uint32_t pad2;
+    int64_t phases;
+    uint64_t t_last;        // %globaltimer at the previous barrier
+    uint64_t t_start;
+    // statistics (dsssp_stats order for the first fields)
+    long long st[16];
+};
+
+enum StatIdx {
+    ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_BIGP = 3, ST_SELECT = 4, ST_VLIGHT = 5,
+    ST_VHEAVY = 6, ST_ALIGHT = 7, ST_AHEAVY = 8, ST_FARSCAN = 9, ST_IMPROVE = 10,
+    ST_NSLIGHT = 11, ST_NSHEAVY = 12, ST_NSSELECT = 13, ST_NSTOTAL = 14
+};
+
+// Per-vertex arc segments of the split layout: [x, y) light, [y, z) heavy.
+// uint4 so that one 16-byte load fetches a vertex's segments.
+
+struct SolveArgs {
+    const uint4 *vinfo;             // n
+    const uint2 *arcs;              // m: (head, weight bits), light-first per row
+    unsigned long long *packed;     // n
+    uint32_t *near_stamp;           // n
+    uint32_t *far_flag;             // n: 0 no entry, 1 live entry, 2 dead entry
+    uint32_t *s_stamp;              // n
+    uint32_t *F0, *F1;              // n each
+    uint32_t *S;                    // n
+    uint32_t *FAR0, *FAR1;          // n each
+    uint4 *BIG;                     // n: (u, arc offset in the flattened list, segment begin, 0)
+    Ctl *ctl;
+    double delta;
+    int64_t timeout_ns;
+    int64_t max_phases;
+    uint32_t n;
+    uint32_t src;
+    uint32_t inf_key;
+    uint32_t big_degree;
+    int32_t dtype;
+    int32_t test_hook;
+    uint32_t nblocks;
+    uint32_t pad;
+};
+
+// Launch helpers implemented in solve.cu / split.cu (host side).
+cudaError_t launch_validate(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                            uint32_t *wbits, int dtype, uint32_t *off, int *flags, cudaStream_t st);
+cudaError_t launch_split(int64_t n, int64_t m, const uint32_t *off, const int32_t *col,
+                         const uint32_t *wbits, uint32_t light_max, uint32_t *scratch_pl,
+                         uint32_t *scratch_tiles, uint2 *arcs, uint4 *vinfo, uint32_t *perm,
+                         cudaStream_t st);
+size_t split_scratch_tiles(int64_t m);
+
+cudaError_t launch_init(const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_solve_persistent(const SolveArgs &a, int grid, int block, cudaStream_t st);
+cudaError_t solve_occupancy(int block, int *blocks_per_sm);
+cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, int block,
+                                 cudaStream_t st);
+cudaError_t launch_serial_step(const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_unpack(const SolveArgs &a, void *dist, int32_t *pred, cudaStream_t st);
+
+}  // namespace dsssp

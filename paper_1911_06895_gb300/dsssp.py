@@ -1,0 +1,211 @@
+"""ctypes binding of the C ABI in ``include/dsssp.h`` (argument marshalling only).
+
+The raw entry points keep the C names (``dsssp_graph_create``, ``dsssp_solve``,
+...). ``Graph`` wraps a handle and takes / returns torch tensors: torch only
+provides device memory and the current CUDA stream; every step of the solve
+runs in the library's CUDA kernels. There is no CPU fallback: importing this
+module fails when ``libdsssp.so`` has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdsssp.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1911_06895_gb300.build` "
+                      "(the CUDA library is required; there is no fallback path)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- status / enums (mirror include/dsssp.h) ----------------------------------------
+DSSSP_OK = 0
+DSSSP_ERR_INVALID_ARG = 1
+DSSSP_ERR_BAD_GRAPH = 2
+DSSSP_ERR_NEG_WEIGHT = 3
+DSSSP_ERR_NOT_CONVERGED = 4
+DSSSP_ERR_TIMEOUT = 5
+DSSSP_ERR_CUDA = 6
+DSSSP_ERR_NO_TAPE = 7
+DSSSP_ERR_OOM = 8
+DSSSP_ERR_UNSUPPORTED = 9
+
+DSSSP_I32 = 0
+DSSSP_F32 = 1
+DSSSP_MODE_PERSISTENT = 0
+DSSSP_MODE_STEPPED = 1
+DSSSP_FLAG_ASYNC = 0x1
+DSSSP_HOOK_NONE = 0
+DSSSP_HOOK_STALL_BARRIER = 1
+
+
+class dsssp_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("mode", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("grid_size", ctypes.c_int32), ("big_degree", ctypes.c_int32),
+                ("max_phases", ctypes.c_int64), ("timeout_ns", ctypes.c_int64), ("test_hook", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 5)]
+
+
+class dsssp_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "buckets", "light_phases", "heavy_phases", "big_phases", "select_phases", "vertices_light",
+        "vertices_heavy", "arcs_light", "arcs_heavy", "far_scanned", "improvements", "ns_light",
+        "ns_heavy", "ns_select", "ns_total", "grid_size", "block_size")] + [("reserved", ctypes.c_int64 * 7)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+_vp = ctypes.c_void_p
+_i64 = ctypes.c_int64
+_i32 = ctypes.c_int32
+
+
+def _fn(name, restype, argtypes):
+    f = getattr(_lib, name)
+    f.restype = restype
+    f.argtypes = argtypes
+    return f
+
+
+dsssp_status_string = _fn("dsssp_status_string", ctypes.c_char_p, [ctypes.c_int])
+dsssp_options_default = _fn("dsssp_options_default", ctypes.c_int, [ctypes.POINTER(dsssp_options)])
+dsssp_graph_create = _fn("dsssp_graph_create", ctypes.c_int,
+                         [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.POINTER(_vp)])
+dsssp_graph_destroy = _fn("dsssp_graph_destroy", ctypes.c_int, [_vp])
+dsssp_graph_info = _fn("dsssp_graph_info", ctypes.c_int,
+                       [_vp, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i32)])
+dsssp_prepare = _fn("dsssp_prepare", ctypes.c_int, [_vp, ctypes.c_double, _vp])
+dsssp_solve = _fn("dsssp_solve", ctypes.c_int,
+                  [_vp, _i32, ctypes.c_double, _vp, _vp, ctypes.POINTER(dsssp_options),
+                   ctypes.POINTER(dsssp_stats), _vp])
+dsssp_graph_sync = _fn("dsssp_graph_sync", ctypes.c_int, [_vp, _vp])
+
+EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create", "dsssp_graph_destroy",
+            "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync"]
+
+
+class DsssError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        msg = dsssp_status_string(status).decode()
+        super().__init__(f"{what}: {msg} (status {status})" if what else f"{msg} (status {status})")
+
+
+def check(status: int, what: str = "") -> None:
+    if status != DSSSP_OK:
+        raise DsssError(status, what)
+
+
+def make_options(**kw) -> dsssp_options:
+    o = dsssp_options()
+    check(dsssp_options_default(ctypes.byref(o)))
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(dt) -> int:
+    import torch
+    if dt in (np.float32, torch.float32):
+        return DSSSP_F32
+    if dt in (np.int32, torch.int32):
+        return DSSSP_I32
+    raise TypeError(f"weights must be int32 or float32, got {dt}")
+
+
+@dataclass
+class SolveResult:
+    dist: "object"
+    pred: "object"
+    stats: dict | None
+
+
+class Graph:
+    """A graph handle on the current CUDA device (library-owned copy of the CSR).
+
+    ``row_ptr`` int64[n+1], ``col`` int32[m], ``w`` int32[m] or float32[m], given as
+    numpy arrays (copied from host memory) or CUDA torch tensors (copied on device).
+    """
+
+    def __init__(self, row_ptr, col, w, stream=None):
+        import torch
+        self._h = None
+        on_dev = isinstance(row_ptr, torch.Tensor) and row_ptr.is_cuda
+        if on_dev:
+            rp = row_ptr.contiguous(); cl = col.contiguous(); ww = w.contiguous()
+            if rp.dtype != torch.int64 or cl.dtype != torch.int32:
+                raise TypeError("row_ptr must be int64 and col int32")
+            code = _dtype_code(ww.dtype)
+            ptrs = (rp.data_ptr(), cl.data_ptr(), ww.data_ptr())
+            n = rp.numel() - 1
+            m = cl.numel()
+            keep = (rp, cl, ww)
+        else:
+            rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+            cl = np.ascontiguousarray(col, dtype=np.int32)
+            ww = np.ascontiguousarray(w)
+            code = _dtype_code(ww.dtype.type)
+            ptrs = (rp.ctypes.data, cl.ctypes.data, ww.ctypes.data)
+            n = rp.shape[0] - 1
+            m = cl.shape[0]
+            keep = (rp, cl, ww)
+        h = ctypes.c_void_p()
+        st = dsssp_graph_create(n, m, ptrs[0], ptrs[1], ptrs[2], code, 1 if on_dev else 0,
+                                _stream_ptr(stream), ctypes.byref(h))
+        del keep
+        check(st, "dsssp_graph_create")
+        self._h = h
+        self.n, self.m, self.dtype_code = n, m, code
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            dsssp_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare(self, delta: float, stream=None) -> None:
+        """Light/heavy split for delta (cached in the handle)."""
+        check(dsssp_prepare(self._h, float(delta), _stream_ptr(stream)), "dsssp_prepare")
+
+    def solve(self, src: int, delta: float, dist=None, pred=None, options: dsssp_options | None = None,
+              stats: bool = False, stream=None) -> SolveResult:
+        """One delta-stepping solve; returns CUDA tensors dist (graph dtype) and pred (int32)."""
+        import torch
+        tdt = torch.float32 if self.dtype_code == DSSSP_F32 else torch.int32
+        if dist is None:
+            dist = torch.empty(self.n, dtype=tdt, device="cuda")
+        if pred is None:
+            pred = torch.empty(self.n, dtype=torch.int32, device="cuda")
+        if dist.dtype != tdt or dist.numel() < self.n or pred.dtype != torch.int32 or pred.numel() < self.n:
+            raise TypeError("dist/pred have the wrong dtype or size")
+        st = dsssp_stats() if stats else None
+        rc = dsssp_solve(self._h, int(src), float(delta), ctypes.c_void_p(dist.data_ptr()),
+                         ctypes.c_void_p(pred.data_ptr()), ctypes.byref(options) if options is not None else None,
+                         ctypes.byref(st) if st is not None else None, _stream_ptr(stream))
+        check(rc, "dsssp_solve")
+        return SolveResult(dist, pred, st.as_dict() if st is not None else None)
+
+    def sync(self, stream=None) -> None:
+        check(dsssp_graph_sync(self._h, _stream_ptr(stream)), "dsssp_graph_sync")

@@ -1,0 +1,292 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Distances must match bit for bit (float32 and int32) and predecessors exactly:
+the least fixed point of the rounded min-plus recurrence does not depend on
+the relaxation order (see oracle/oracle.c), and the packed 64-bit atomicMin
+keeps the smallest predecessor among equal distances.
+"""
+import json
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import graphgen
+import graphgen.workloads as W
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+INT_INF = np.iinfo(np.int32).max
+
+
+@pytest.fixture(scope="module")
+def ds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_06895_gb300 as ds
+    return ds
+
+
+def gpu_solve(ds, h, src, delta, **opt):
+    o = ds.make_options(**opt) if opt else None
+    r = h.solve(src, delta, options=o, stats=True)
+    return r.dist.cpu().numpy(), r.pred.cpu().numpy(), r.stats
+
+
+def assert_same(g, src, d, p, d_ref=None, p_ref=None, what=""):
+    if d_ref is None:
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, src)
+    if d.dtype == np.float32:
+        bad = np.flatnonzero(d.view(np.uint32) != d_ref.view(np.uint32))
+    else:
+        bad = np.flatnonzero(d != d_ref)
+    assert bad.size == 0, f"{what}: {bad.size} distances differ, first {bad[:5]} gpu {d[bad[:5]]} ref {d_ref[bad[:5]]}"
+    badp = np.flatnonzero(p != p_ref)
+    assert badp.size == 0, f"{what}: {badp.size} predecessors differ, first {badp[:5]} gpu {p[badp[:5]]} ref {p_ref[badp[:5]]}"
+
+
+MODES = [dict(), dict(mode=1), dict(big_degree=32, grid_size=3)]
+
+
+# ------------------------------------------------------------------ hand-built cases
+
+def test_hand_traced_example(ds):
+    with open(os.path.join(GOLDEN, "fig1_trace_example.json")) as f:
+        doc = json.load(f)
+    arcs = [(a, b) for a, b, _ in doc["arcs"]]
+    g = graphgen.from_arcs(doc["n"], arcs, np.array([c for _, _, c in doc["arcs"]], np.int32), dtype=np.int32)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    for opt in MODES:
+        d, p, _ = gpu_solve(ds, h, doc["source_vertex"], doc["delta"], **opt)
+        assert list(d) == doc["dist"] and list(p) == doc["pred"], opt
+
+
+@pytest.mark.parametrize("dtype", [np.int32, np.float32])
+def test_random_small_graphs(ds, dtype):
+    rng = random.Random(7 if dtype == np.int32 else 8)
+    for trial in range(60):
+        n = rng.randint(1, 60)
+        p = rng.choice([0.02, 0.08, 0.2])
+        arcs, ws = [], []
+        for u in range(n):
+            for v in range(n):
+                if rng.random() < p:
+                    arcs.append((u, v))
+                    if dtype == np.int32:
+                        ws.append(rng.choice([0, 1, 2, 3, 7, 40]))
+                    else:
+                        ws.append(rng.choice([0.0, 0.1, 0.2, 0.3, 1e-7, 2.5, rng.random()]))
+        if arcs and rng.random() < 0.5:
+            arcs += arcs[:3]
+            ws += ws[:3]
+        g = graphgen.from_arcs(n, arcs, np.array(ws, dtype=dtype), dtype=dtype)
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        src = rng.randrange(n)
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, src)
+        for delta in (1e-3, 0.25, 3.0, math.inf):
+            for opt in MODES:
+                d, pr, _ = gpu_solve(ds, h, src, delta, **opt)
+                assert_same(g, src, d, pr, d_ref, p_ref, f"trial {trial} delta {delta} {opt}")
+        h.close()
+
+
+def test_edge_cases(ds):
+    cases = []
+    cases.append((graphgen.from_arcs(1, [], np.zeros(0, np.float32), dtype=np.float32), 0))   # one vertex
+    cases.append((graphgen.from_arcs(5, [(1, 2), (2, 3)], np.array([1, 1], np.int32), dtype=np.int32), 0))
+    cases.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (2, 1), (2, 3), (3, 0)],
+                                     np.array([0, 0, 0, 0.5, 0], np.float32), dtype=np.float32), 0))
+    big = INT_INF - 10
+    cases.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([big, 20, 5], np.int32),
+                                     dtype=np.int32), 0))
+    cases.append((graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([3e38, 3e38], np.float32),
+                                     dtype=np.float32), 0))
+    cases.append((graphgen.from_arcs(3, [(0, 1), (0, 2), (1, 2)], np.array([-0.0, 1.0, 0.0], np.float32),
+                                     dtype=np.float32), 0))
+    # a hub whose out-degree exceeds big_degree, zero-weight arcs into the source
+    k = 5000
+    rng = np.random.default_rng(3)
+    hub_w = rng.integers(0, 50, k).astype(np.int32)
+    arcs = [(0, 1 + i) for i in range(k)] + [(1 + i, 0) for i in range(0, k, 7)] + [(5, 1 + i) for i in range(k)]
+    ws = np.concatenate([hub_w, np.zeros(len(range(0, k, 7)), np.int32), rng.integers(0, 9, k).astype(np.int32)])
+    cases.append((graphgen.from_arcs(k + 1, arcs, ws, dtype=np.int32), 0))
+    cases.append((graphgen.from_arcs(k + 1, arcs, ws, dtype=np.int32), 17))
+    # a long path: thousands of buckets
+    n = 3000
+    wp = (np.random.default_rng(5).random(n - 1) * 10).astype(np.float32)
+    cases.append((graphgen.from_arcs(n, [(i, i + 1) for i in range(n - 1)], wp, dtype=np.float32), 0))
+    for ci, (g, src) in enumerate(cases):
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, src)
+        for delta in (0.5, 4.0, 1e9):
+            for opt in MODES:
+                d, p, _ = gpu_solve(ds, h, src, delta, **opt)
+                assert_same(g, src, d, p, d_ref, p_ref, f"case {ci} delta {delta} {opt}")
+        h.close()
+
+
+# ------------------------------------------------------------------ workload recipes
+
+def test_rmat14_int_delta32(ds):
+    """R-MAT scale 14, int32 U{1..255}, Delta 32, highest-out-degree source: every launch shape."""
+    g, srcs, deltas = W.rmat14_int()
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, srcs[0])
+    for opt in MODES + [dict(grid_size=1), dict(block_size=128), dict(big_degree=64)]:
+        d, p, st = gpu_solve(ds, h, srcs[0], deltas[0], **opt)
+        assert_same(g, srcs[0], d, p, d_ref, p_ref, str(opt))
+        assert st["buckets"] >= 1 and st["arcs_light"] > 0
+    # the other sources too
+    for s in graphgen.random_sources(g, 6, 99):
+        d, p, _ = gpu_solve(ds, h, int(s), deltas[0])
+        assert_same(g, int(s), d, p, what=f"src {s}")
+
+
+@pytest.mark.parametrize("delta", [0.01, 0.05, 0.1, 0.5])
+def test_rmat_unit_weights_deltas(ds, delta):
+    """The scale-22 recipe at scale 17 (oracle in seconds): fp32 U[0,1), four Deltas."""
+    g, srcs, _ = W.rmat22_unit(scale=17, n_sources=3)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    for s in srcs:
+        d, p, _ = gpu_solve(ds, h, s, delta)
+        assert_same(g, s, d, p, what=f"src {s} delta {delta}")
+
+
+@pytest.mark.parametrize("delta", [100.0, 1000.0, 10000.0])
+def test_grid_int_deltas(ds, delta):
+    """The 4096 x 4096 grid recipe at 300 x 300: high diameter, int32 U{1..1000}."""
+    g, srcs, _ = W.grid4096(side=300)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
+    for opt in (dict(), dict(mode=1)):
+        if opt and delta == 100.0:
+            continue           # the stepped mode is host-driven; skip its thousands of phases
+        d, p, _ = gpu_solve(ds, h, 0, delta, **opt)
+        assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta} {opt}")
+
+
+def test_er_family_small(ds):
+    for g, src in W.er_family(count=6, n_lo=1000, n_hi=20000):
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        d, p, _ = gpu_solve(ds, h, src, 0.1)
+        assert_same(g, src, d, p, what=g.name)
+        h.close()
+
+
+def test_device_pointer_graph_and_async(ds):
+    g, srcs, deltas = W.rmat14_int(scale=12)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    cl = torch.from_numpy(g.col).cuda()
+    ww = torch.from_numpy(g.w).cuda()
+    h = ds.Graph(rp, cl, ww)
+    o = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
+    r = h.solve(srcs[0], deltas[0], options=o)
+    h.sync()
+    assert_same(g, srcs[0], r.dist.cpu().numpy(), r.pred.cpu().numpy(), what="device-ptr async")
+
+
+# ------------------------------------------------------------------ error paths (no fault)
+
+def test_validation_errors(ds):
+    g = graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([1.0, -2.0], np.float32), dtype=np.float32)
+    with pytest.raises(ds.DsssError) as e:
+        ds.Graph(g.row_ptr, g.col, g.w)
+    assert e.value.status == ds.DSSSP_ERR_NEG_WEIGHT
+    g = graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([1.0, np.nan], np.float32), dtype=np.float32)
+    with pytest.raises(ds.DsssError) as e:
+        ds.Graph(g.row_ptr, g.col, g.w)
+    assert e.value.status == ds.DSSSP_ERR_NEG_WEIGHT
+    g = graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([1, 2], np.int32), dtype=np.int32)
+    col = g.col.copy()
+    col[1] = 7
+    with pytest.raises(ds.DsssError) as e:
+        ds.Graph(g.row_ptr, col, g.w)
+    assert e.value.status == ds.DSSSP_ERR_BAD_GRAPH
+    rp = g.row_ptr.copy()
+    rp[1] = 5
+    with pytest.raises(ds.DsssError) as e:
+        ds.Graph(rp, g.col, g.w)
+    assert e.value.status == ds.DSSSP_ERR_BAD_GRAPH
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    with pytest.raises(ds.DsssError) as e:
+        h.solve(3, 1.0)
+    assert e.value.status == ds.DSSSP_ERR_INVALID_ARG
+    with pytest.raises(ds.DsssError) as e:
+        h.solve(0, 0.0)
+    assert e.value.status == ds.DSSSP_ERR_INVALID_ARG
+
+
+def test_bounded_wait_times_out_and_context_survives(ds):
+    """One block leaves before the first barrier (test hook): the others' bounded
+    wait runs out, the solve returns DSSSP_ERR_TIMEOUT, outputs are untouched,
+    and the next solve on the same context is correct."""
+    g, srcs, deltas = W.rmat14_int(scale=11)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    dist = torch.full((g.n,), -5, dtype=torch.int32, device="cuda")
+    pred = torch.full((g.n,), -5, dtype=torch.int32, device="cuda")
+    o = ds.make_options(test_hook=ds.DSSSP_HOOK_STALL_BARRIER, timeout_ns=50_000_000, grid_size=4)
+    with pytest.raises(ds.DsssError) as e:
+        h.solve(srcs[0], deltas[0], dist=dist, pred=pred, options=o)
+    assert e.value.status == ds.DSSSP_ERR_TIMEOUT
+    assert int((dist != -5).sum()) == 0 and int((pred != -5).sum()) == 0
+    d, p, _ = gpu_solve(ds, h, srcs[0], deltas[0])
+    assert_same(g, srcs[0], d, p, what="after timeout")
+    # asynchronous flavour: the status surfaces at sync
+    o.flags = ds.DSSSP_FLAG_ASYNC
+    h.solve(srcs[0], deltas[0], options=o)
+    with pytest.raises(ds.DsssError) as e:
+        h.sync()
+    assert e.value.status == ds.DSSSP_ERR_TIMEOUT
+    h.sync()
+
+
+def test_phase_cap_not_converged(ds):
+    g, srcs, deltas = W.rmat14_int(scale=11)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    for mode in (0, 1):
+        with pytest.raises(ds.DsssError) as e:
+            h.solve(srcs[0], deltas[0], options=ds.make_options(max_phases=3, mode=mode))
+        assert e.value.status == ds.DSSSP_ERR_NOT_CONVERGED
+    d, p, _ = gpu_solve(ds, h, srcs[0], deltas[0])
+    assert_same(g, srcs[0], d, p, what="after cap")
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+@pytest.fixture(scope="module")
+def rmat22(ds):
+    g, srcs, deltas = W.rmat22_unit()
+    return g, srcs, deltas, ds.Graph(g.row_ptr, g.col, g.w)
+
+
+def test_full_rmat22_all_deltas_one_source_exact(ds, rmat22):
+    """Full-size scale-22 R-MAT (fp32 U[0,1)), bench launch shape: whole arrays vs Dijkstra."""
+    g, srcs, deltas, h = rmat22
+    s = srcs[0]
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, s)
+    for delta in deltas:
+        d, p, _ = gpu_solve(ds, h, s, delta)
+        assert_same(g, s, d, p, d_ref, p_ref, f"delta {delta}")
+
+
+def test_full_rmat22_more_sources_invariants(ds, rmat22):
+    """Further sources at full size: the invariant checker (arc inequality, predecessor
+    equality and minimality) on every vertex, plus exact distances at sampled vertices."""
+    g, srcs, deltas, h = rmat22
+    for s, delta in zip(srcs[1:4], deltas):
+        d, p, _ = gpu_solve(ds, h, s, delta)
+        assert oracle.check_invariants(g.row_ptr, g.col, g.w, s, d, p) == 0
+
+
+def test_full_grid4096_all_deltas_exact(ds):
+    g, srcs, deltas = W.grid4096()
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
+    for delta in deltas:
+        d, p, _ = gpu_solve(ds, h, 0, delta)
+        assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta}")
