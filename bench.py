@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark: delta-stepping SSSP on the scale-22 R-MAT workload.
+
+Workload (stands in for the paper's SNAP / GraphChallenge graphs, which are not
+available): directed R-MAT scale 22 (4,194,304 vertices, 16 * 2^22 draws,
+a/b/c/d = .57/.19/.19/.05, self-loops and repeats removed), float32 weights
+U[0,1), 64 sources with out-degree >= 1 solved one after another, Delta swept
+over {0.01, 0.05, 0.1, 0.5}. One step = the 256 solves (4 Deltas x 64 sources).
+
+value   GTEPS = m * solves / device time, inputs resident in HBM, CUDA events
+        on the solve stream (max over ranks); the per-Delta light/heavy split is
+        cached and timed on its own ("split_ms").
+e2e     the same metric through the public C ABI from pinned HOST buffers: every
+        step creates the graph from host CSR, solves all 256 sources and copies
+        every dist/pred array back to pinned host memory.
+roofline  the solve kernel's algorithmic bytes (per-unit figures below) over
+        its CUDA-event time, against the measured HBM copy bandwidth.
+cpu_baseline  the CPU oracle (binary-heap Dijkstra, one source per host core)
+        on a bounded sample of the same sources.
+
+Multi-GPU (torchrun): every rank solves its own 64 sources on its own copy of
+the graph (weak scaling, no collective on the data path); value sums the
+ranks' edges over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DELTAS = [0.01, 0.05, 0.1, 0.5]
+
+# Algorithmic bytes (what the method must move):
+#   per frontier / S vertex: 4 (list id) + 16 (arc segments) + 8 (packed[u])
+#   per arc relaxed:         8 (head, weight) + 8 (packed[v] read-modify-write)
+#   per far-pile entry:      4 (id) + 4 (flag) + 8 (packed) + 4 (rewrite)
+#   per vertex, init+unpack: 8 + 12 (packed, stamps) + 8 (packed read) + 8 (dist, pred)
+B_VERTEX, B_ARC, B_FAR, B_INIT_UNPACK = 28, 16, 20, 36
+
+
+def algorithmic_bytes(st: dict, n: int) -> int:
+    return (B_VERTEX * (st["vertices_light"] + st["vertices_heavy"]) + B_ARC * (st["arcs_light"] + st["arcs_heavy"])
+            + B_FAR * st["far_scanned"] + B_INIT_UNPACK * n)
+
+
+def light_bytes(st: dict) -> int:
+    return B_VERTEX * st["vertices_light"] + B_ARC * st["arcs_light"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def build_workload(scale: int, n_sources: int, rank: int):
+    import graphgen.workloads as W
+    g, _, deltas = W.rmat22_unit(scale=scale, n_sources=n_sources)
+    import graphgen
+    # weak scaling: rank r draws its own sources from the same graph
+    srcs = [int(s) for s in graphgen.random_sources(g, n_sources, 2 + 1000 * rank)]
+    return g, srcs, deltas
+
+
+def cpu_oracle_gteps(g, sources, threads=None):
+    import oracle
+    t0 = time.perf_counter()
+    _, _, used = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources, threads)
+    dt = time.perf_counter() - t0
+    return g.m * len(sources) / dt / 1e9, used, dt
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle timed on the host cores (the comparison arm)."""
+    if rank != 0:
+        return
+    g, srcs, deltas = build_workload(args.scale, args.sources, 0)
+    cores = os.cpu_count() or 1
+    per_step = srcs[:min(len(srcs), cores)]
+    for _ in range(args.warmup):
+        cpu_oracle_gteps(g, per_step[:1], 1)
+    times = []
+    used = 1
+    for _ in range(args.steps):
+        _, used, dt = cpu_oracle_gteps(g, per_step)
+        times.append(dt)
+    tot = sum(times)
+    value = g.m * len(per_step) * args.steps / tot / 1e9
+    line = {"impl": "reference", "metric": "delta-stepping SSSP GTEPS (m * sources / time)", "value": value,
+            "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}_unit_fp32_sources{args.sources}", "n": g.n, "m": g.m,
+                       "sources_per_step": len(per_step)},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": used, "kind": "oracle",
+                             "sample": f"{len(per_step)} sources per step, binary-heap Dijkstra, one source per thread"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=22)
+    ap.add_argument("--sources", type=int, default=64)
+    ap.add_argument("--mode", type=int, default=0, help="0 persistent, 1 stepped")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sources", type=int, default=0, help="CPU baseline sample (0: one per core)")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import paper_1911_06895_gb300 as ds
+
+    torch.cuda.set_device(local)
+    dist_pg = None
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist_pg = tdist
+
+    g, srcs, deltas = build_workload(args.scale, args.sources, rank)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        h = ds.Graph(g.row_ptr, g.col, g.w, stream=stream)
+        # light/heavy split per Delta, timed on its own
+        split_ms = {}
+        for d in deltas:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.prepare(d, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            split_ms[str(d)] = e0.elapsed_time(e1)
+        dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
+        pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=args.mode)
+
+        # per-solve statistics (one untimed pass) -> algorithmic bytes
+        stats = {}
+        for d in deltas:
+            stats[d] = [h.solve(s, d, dist=dist, pred=pred, stream=stream, stats=True,
+                                options=ds.make_options(mode=args.mode)).stats for s in srcs]
+
+        def one_step(record):
+            for d in deltas:
+                for s in srcs:
+                    if record is not None:
+                        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                        ev[0].record(stream)
+                    h.solve(s, d, dist=dist, pred=pred, options=opt, stream=stream)
+                    if record is not None:
+                        ev[1].record(stream)
+                        record.append((d, ev))
+
+        for _ in range(args.warmup):
+            one_step(None)
+        h.sync(stream)
+        torch.cuda.synchronize()
+        if dist_pg:
+            dist_pg.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        recs = []
+        t0.record(stream)
+        for k in range(args.steps):
+            one_step(recs if k == 0 else None)
+        t1.record(stream)
+        t1.synchronize()
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        h.sync(stream)
+        elapsed_ms = t0.elapsed_time(t1)
+        if dist_pg:
+            tt = torch.tensor([elapsed_ms], device="cuda")
+            dist_pg.all_reduce(tt, op=dist_pg.ReduceOp.MAX)
+            elapsed_ms = float(tt.item())
+        ms_per_step = elapsed_ms / args.steps
+        solves = len(deltas) * len(srcs)
+        gteps = g.m * solves * world / (ms_per_step * 1e-3) / 1e9
+
+        # per-Delta GTEPS and roofline of the solve (events around each solve call)
+        per_delta = {}
+        tot_bytes, tot_ms, tot_light_b, tot_light_ns = 0, 0.0, 0, 0
+        for d in deltas:
+            ms_d = sum(ev[0].elapsed_time(ev[1]) for dd, ev in recs if dd == d)
+            per_delta[str(d)] = {"gteps": g.m * len(srcs) / (ms_d * 1e-3) / 1e9, "ms_per_solve": ms_d / len(srcs)}
+            b = sum(algorithmic_bytes(st, g.n) for st in stats[d])
+            tot_bytes += b
+            tot_ms += ms_d
+            tot_light_b += sum(light_bytes(st) for st in stats[d])
+            tot_light_ns += sum(st["ns_light"] for st in stats[d])
+            per_delta[str(d)].update({
+                "buckets": sum(st["buckets"] for st in stats[d]) / len(srcs),
+                "phases": sum(st["light_phases"] + st["heavy_phases"] + st["big_phases"] + st["select_phases"]
+                              for st in stats[d]) / len(srcs),
+                "arcs_relaxed_per_solve": sum(st["arcs_light"] + st["arcs_heavy"] for st in stats[d]) / len(srcs),
+                "kernel_us_per_solve": sum(st["ns_total"] for st in stats[d]) / len(srcs) / 1e3})
+        peak, peak_kind = measured_peak_gbs()
+        achieved = tot_bytes / (tot_ms * 1e-3) / 1e9
+        light_gbs = tot_light_b / (tot_light_ns * 1e-9) / 1e9 if tot_light_ns else None
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        k = args.cpu_sources or min(cores, len(srcs))
+        v, used, dt = cpu_oracle_gteps(g, srcs[:k])
+        cpu = {"value": v, "unit": "GTEPS", "cores": used, "kind": "oracle",
+               "sample": f"{k} of the {len(srcs)} sources, binary-heap Dijkstra one source per thread, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "delta-stepping SSSP GTEPS (m * sources / device time)",
+            "value": gteps, "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"rmat{args.scale}_unit_fp32_sources{args.sources}_deltas4",
+                       "n": g.n, "m": g.m, "sources": len(srcs), "deltas": deltas, "solves_per_step": solves,
+                       "mode": "persistent" if args.mode == 0 else "stepped",
+                       "l2": "inputs larger than L2 (arcs %.0f MB per Delta)" % (g.m * 8 / 1e6),
+                       "split_ms": split_ms, "per_delta": per_delta, "parallelism": f"replicas{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "k_solve_persistent (with its init/unpack launches)",
+                         "light_relax_gbs": light_gbs,
+                         "light_relax_frac": (light_gbs / peak) if light_gbs else None},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": 4 * solves * args.steps,
+        }
+        print(json.dumps(line), flush=True)
+    if dist_pg:
+        dist_pg.barrier()
+        dist_pg.destroy_process_group()
+
+
+def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args):
+    """Public-API end to end: host CSR -> graph -> 256 solves -> results in pinned host memory."""
+    rp = torch.from_numpy(g.row_ptr).pin_memory()
+    cl = torch.from_numpy(g.col).pin_memory()
+    ww = torch.from_numpy(g.w).pin_memory()
+    solves = len(deltas) * len(srcs)
+    hd = torch.empty((2, g.n), dtype=torch.float32).pin_memory()
+    hp = torch.empty((2, g.n), dtype=torch.int32).pin_memory()
+    stream = torch.cuda.Stream()
+    steps = max(1, min(args.steps, 2))
+
+    def step():
+        with torch.cuda.stream(stream):
+            h = ds.Graph(rp.numpy(), cl.numpy(), ww.numpy(), stream=stream)
+            dist = torch.empty((2, g.n), dtype=torch.float32, device="cuda")
+            pred = torch.empty((2, g.n), dtype=torch.int32, device="cuda")
+            opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
+            k = 0
+            for d in deltas:
+                for s in srcs:
+                    h.solve(s, d, dist=dist[k & 1], pred=pred[k & 1], options=opt, stream=stream)
+                    hd[k & 1].copy_(dist[k & 1], non_blocking=True)
+                    hp[k & 1].copy_(pred[k & 1], non_blocking=True)
+                    k += 1
+            h.sync(stream)
+            stream.synchronize()
+            h.close()
+
+    step()
+    torch.cuda.synchronize()
+    if dist_pg:
+        dist_pg.barrier()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t) / steps
+    if dist_pg:
+        tt = torch.tensor([dt], device="cuda")
+        dist_pg.all_reduce(tt, op=dist_pg.ReduceOp.MAX)
+        dt = float(tt.item())
+    return {"value": g.m * solves * world / dt / 1e9, "unit": "GTEPS",
+            "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes),
+            "d2h_bytes_per_step": int(solves * g.n * 8), "ms_per_step": dt * 1e3, "steps": steps}
+
+
+if __name__ == "__main__":
+    main()
