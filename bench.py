@@ -272,7 +272,7 @@ def main():
             tot_light_ns += sum(st["ns_light"] for st in stats[d])
             per_delta[str(d)].update({
                 "buckets": sum(st["buckets"] for st in stats[d]) / len(srcs),
-                "phases": sum(st["light_phases"] + st["heavy_phases"] + st["big_phases"] + st["select_phases"]
+                "phases": sum(st["light_phases"] + st["heavy_phases"] + st["select_phases"]
                               for st in stats[d]) / len(srcs),
                 "arcs_relaxed_per_solve": sum(st["arcs_light"] + st["arcs_heavy"] for st in stats[d]) / len(srcs),
                 "kernel_us_per_solve": sum(st["ns_total"] for st in stats[d]) / len(srcs) / 1e3})

@@ -85,8 +85,7 @@ typedef struct {
     int32_t  mode;          /* dsssp_mode; default DSSSP_MODE_PERSISTENT                        */
     int32_t  block_size;    /* threads per block, multiple of 32, <= 512; default 512           */
     int32_t  grid_size;     /* blocks of the persistent kernel; default = all co-resident blocks */
-    int32_t  big_degree;    /* arc segments longer than this are spread over the whole grid;
-                               default 512                                                        */
+    int32_t  reserved0;     /* must be 0                                                         */
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
@@ -99,7 +98,6 @@ typedef struct {
     int64_t buckets;          /* non-empty buckets processed                                   */
     int64_t light_phases;     /* light relaxation rounds (inner loop of Fig. 1)                */
     int64_t heavy_phases;     /* heavy passes                                                   */
-    int64_t big_phases;       /* grid-wide passes over long arc segments                       */
     int64_t select_phases;    /* next-bucket searches (far-pile compactions)                   */
     int64_t vertices_light;   /* sum of |frontier| over light rounds                           */
     int64_t vertices_heavy;   /* sum of |S| over heavy passes                                   */
@@ -107,13 +105,13 @@ typedef struct {
     int64_t arcs_heavy;       /* heavy arcs relaxed                                             */
     int64_t far_scanned;      /* far-pile entries examined by next-bucket searches             */
     int64_t improvements;     /* strict distance decreases                                      */
-    int64_t ns_light;         /* device time in light rounds (incl. their long-segment passes) */
+    int64_t ns_light;         /* device time in light rounds                                    */
     int64_t ns_heavy;         /* device time in heavy passes                                    */
     int64_t ns_select;        /* device time in next-bucket searches                           */
     int64_t ns_total;         /* device time of the whole solve kernel                          */
     int64_t grid_size;        /* blocks used                                                    */
     int64_t block_size;       /* threads per block used                                          */
-    int64_t reserved[7];
+    int64_t reserved[8];
 } dsssp_stats;
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -138,12 +138,12 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     const size_t o_near = bytes;   bytes += up(n * 4);
     const size_t o_far = bytes;    bytes += up(n * 4);
     const size_t o_s = bytes;      bytes += up(n * 4);
-    const size_t o_f0 = bytes;     bytes += up(n * 4);
-    const size_t o_f1 = bytes;     bytes += up(n * 4);
-    const size_t o_S = bytes;      bytes += up(n * 4);
+    const size_t o_f0 = bytes;     bytes += up(n * 16);
+    const size_t o_f1 = bytes;     bytes += up(n * 16);
+    const size_t o_s0 = bytes;     bytes += up(n * 16);
+    const size_t o_s1 = bytes;     bytes += up(n * 16);
     const size_t o_far0 = bytes;   bytes += up(n * 4);
     const size_t o_far1 = bytes;   bytes += up(n * 4);
-    const size_t o_big = bytes;    bytes += up(n * 16);
     const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
     const size_t o_sticky = bytes; bytes += up(sizeof(int32_t));
     char *base = nullptr;
@@ -157,12 +157,12 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     a.near_stamp = (uint32_t *)(base + o_near);
     a.far_flag = (uint32_t *)(base + o_far);
     a.s_stamp = (uint32_t *)(base + o_s);
-    a.F0 = (uint32_t *)(base + o_f0);
-    a.F1 = (uint32_t *)(base + o_f1);
-    a.S = (uint32_t *)(base + o_S);
+    a.F0 = (uint4 *)(base + o_f0);
+    a.F1 = (uint4 *)(base + o_f1);
+    a.S0 = (uint4 *)(base + o_s0);
+    a.S1 = (uint4 *)(base + o_s1);
     a.FAR0 = (uint32_t *)(base + o_far0);
     a.FAR1 = (uint32_t *)(base + o_far1);
-    a.BIG = (uint4 *)(base + o_big);
     a.ctl = (Ctl *)(base + o_ctl);
     g->ctl = a.ctl;
     g->sticky = (int32_t *)(base + o_sticky);
@@ -174,7 +174,6 @@ void fill_stats(const Ctl &c, int grid, int block, dsssp_stats *s) {
     s->buckets = c.st[ST_BUCKETS];
     s->light_phases = c.st[ST_LIGHT];
     s->heavy_phases = c.st[ST_HEAVY];
-    s->big_phases = c.st[ST_BIGP];
     s->select_phases = c.st[ST_SELECT];
     s->vertices_light = c.st[ST_VLIGHT];
     s->vertices_heavy = c.st[ST_VHEAVY];
@@ -217,7 +216,6 @@ dsssp_status dsssp_options_default(dsssp_options *opt) {
     opt->mode = DSSSP_MODE_PERSISTENT;
     opt->block_size = 512;
     opt->grid_size = 0;
-    opt->big_degree = 512;
     opt->max_phases = (int64_t)1 << 26;
     opt->timeout_ns = 2000000000LL;
     return DSSSP_OK;
@@ -246,7 +244,6 @@ dsssp_status dsssp_graph_create(int64_t n, int64_t m, const int64_t *row_ptr, co
         return fail(DSSSP_ERR_CUDA);
     const size_t mm = m ? (size_t)m : 1;
     int64_t *rp_dev = nullptr;
-    int32_t *col_tmp = nullptr;
     int *flags = nullptr;
     cudaError_t e = cudaSuccess;
     if ((e = cudaMalloc(&g->off, (size_t)(n + 1) * sizeof(uint32_t))) != cudaSuccess) return fail(cuda_status(e));
@@ -261,7 +258,6 @@ dsssp_status dsssp_graph_create(int64_t n, int64_t m, const int64_t *row_ptr, co
         if ((e = cudaMallocAsync(&rp_dev, (size_t)(n + 1) * sizeof(int64_t), st)) != cudaSuccess) return fail(cuda_status(e));
         e = cudaMemcpyAsync(rp_dev, row_ptr, (size_t)(n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     }
-    (void)col_tmp;
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->col, col, (size_t)m * sizeof(int32_t), kind, st);
     if (e == cudaSuccess && m > 0) e = cudaMemcpyAsync(g->wbits, w, (size_t)m * sizeof(uint32_t), kind, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(flags, 0, sizeof(int), st);
@@ -321,13 +317,13 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
         opt.mode = opt_in->mode;
         if (opt_in->block_size) opt.block_size = opt_in->block_size;
         if (opt_in->grid_size) opt.grid_size = opt_in->grid_size;
-        if (opt_in->big_degree) opt.big_degree = opt_in->big_degree;
+        if (opt_in->reserved0) return DSSSP_ERR_INVALID_ARG;
         if (opt_in->max_phases) opt.max_phases = opt_in->max_phases;
         if (opt_in->timeout_ns) opt.timeout_ns = opt_in->timeout_ns;
         opt.test_hook = opt_in->test_hook;
     }
     if (opt.block_size < 32 || opt.block_size > 512 || opt.block_size % 32 != 0) return DSSSP_ERR_INVALID_ARG;
-    if (opt.big_degree < 32 || opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
+    if (opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
     if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED) return DSSSP_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -356,9 +352,9 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     a.timeout_ns = opt.timeout_ns;
     a.max_phases = opt.max_phases;
     a.n = (uint32_t)g->n;
+    a.m = (uint32_t)g->m;
     a.src = (uint32_t)src;
     a.inf_key = key_inf(g->dtype);
-    a.big_degree = (uint32_t)opt.big_degree;
     a.dtype = g->dtype;
     a.test_hook = opt.test_hook;
     a.nblocks = (uint32_t)grid;

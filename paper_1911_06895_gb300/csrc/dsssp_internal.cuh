@@ -98,47 +98,45 @@ __host__ __device__ inline uint32_t light_max_key(int dtype, double delta) {
 // Solver phases. Each phase is one grid-wide step separated by a barrier.
 enum Mode : uint32_t {
     MODE_LIGHT = 0,    // relax light arcs of the frontier F  (t_Req = A_L^T (t o t_Bi))
-    MODE_BIG = 1,      // relax long arc segments found in the previous phase, grid-wide
-    MODE_HEAVY = 2,    // relax heavy arcs of S               (t_Req = A_H^T (t o S))
-    MODE_SELECT = 3,   // next non-empty bucket: compact the far pile into F
-    MODE_DONE = 4
+    MODE_HEAVY = 1,    // relax heavy arcs of S               (t_Req = A_H^T (t o S))
+    MODE_SELECT = 2,   // next non-empty bucket: compact the far pile into F and S
+    MODE_DONE = 3
 };
 
-// Control block in device memory. The phase descriptor is written only by the
-// serial step of a barrier (one thread) and read by every block after it.
+// Work lists F (light segments) and S (heavy segments) hold uint4 entries
+// (vertex, exclusive arc offset of the entry within its list, segment begin, 0).
+// An entry is appended with one 64-bit atomicAdd of (1 << 32 | segment length)
+// on the list's counter, so entry positions and arc offsets are consistent and
+// a phase can split the list's flattened arcs evenly over all warps.
 struct Ctl {
     unsigned int bar_count;
     unsigned int bar_gen;
     // phase descriptor
     uint32_t mode;
-    uint32_t big_kind;      // 0: light segments, 1: heavy segments
-    uint32_t cur;           // frontier list being read (0/1); pushes go to cur^1
+    uint32_t cur;           // F list being read (0/1); F pushes go to cur^1
+    uint32_t scur;          // S list holding the current bucket's S
     uint32_t far_cur;       // far list being read (0/1)
     uint32_t qstamp;        // stamp of pushes into the next frontier
-    uint32_t sround;        // stamp of membership in S
+    uint32_t sround;        // stamp of membership in S[scur]
     uint32_t T;             // key < T  <=>  bucket <= i
     uint32_t pad0;
     int64_t bucket;         // current bucket index i
-    // list lengths (atomics)
-    uint32_t nF[2];
-    uint32_t nS;
+    // list counters: (entries << 32) | arcs
+    unsigned long long ctrF[2];
+    unsigned long long ctrS[2];
     uint32_t nFar[2];
     uint32_t far_min;       // lower bound on the keys of live far-pile entries
-    uint32_t pad1[2];
-    unsigned long long big_ctr;   // (entries << 32) | arcs of the long-segment list
     int32_t err;            // first dsssp_status != OK
-    uint32_t pad2;
     int64_t phases;
     uint64_t t_last;        // %globaltimer at the previous barrier
     uint64_t t_start;
-    // statistics (dsssp_stats order for the first fields)
     long long st[16];
 };
 
 enum StatIdx {
-    ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_BIGP = 3, ST_SELECT = 4, ST_VLIGHT = 5,
-    ST_VHEAVY = 6, ST_ALIGHT = 7, ST_AHEAVY = 8, ST_FARSCAN = 9, ST_IMPROVE = 10,
-    ST_NSLIGHT = 11, ST_NSHEAVY = 12, ST_NSSELECT = 13, ST_NSTOTAL = 14
+    ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_SELECT = 3, ST_VLIGHT = 4, ST_VHEAVY = 5,
+    ST_ALIGHT = 6, ST_AHEAVY = 7, ST_FARSCAN = 8, ST_IMPROVE = 9, ST_NSLIGHT = 10, ST_NSHEAVY = 11,
+    ST_NSSELECT = 12, ST_NSTOTAL = 13
 };
 
 // Per-vertex arc segments of the split layout: [x, y) light, [y, z) heavy.
@@ -151,22 +149,20 @@ struct SolveArgs {
     uint32_t *near_stamp;           // n
     uint32_t *far_flag;             // n: 0 no entry, 1 live entry, 2 dead entry
     uint32_t *s_stamp;              // n
-    uint32_t *F0, *F1;              // n each
-    uint32_t *S;                    // n
+    uint4 *F0, *F1;                 // n each
+    uint4 *S0, *S1;                 // n each
     uint32_t *FAR0, *FAR1;          // n each
-    uint4 *BIG;                     // n: (u, arc offset in the flattened list, segment begin, 0)
     Ctl *ctl;
     double delta;
     int64_t timeout_ns;
     int64_t max_phases;
     uint32_t n;
+    uint32_t m;
     uint32_t src;
     uint32_t inf_key;
-    uint32_t big_degree;
     int32_t dtype;
     int32_t test_hook;
     uint32_t nblocks;
-    uint32_t pad;
 };
 
 // Launch helpers implemented in solve.cu / split.cu (host side).

@@ -2,26 +2,31 @@
 //
 // One solve is a sequence of grid-wide phases:
 //   LIGHT   relax the light arcs of the frontier F (the vertices of bucket i
-//           with unrelaxed distances): t_Req = A_L^T (t o t_Bi), fused with the
-//           re-introduction filter and t = min(t, t_Req) (Section IV-C, and the
-//           fusion of Section VI-B) through one 64-bit atomicMin per arc on
-//           packed[v] = key(t[v]) << 32 | pred[v];
-//   BIG     the same relaxation for arc segments longer than big_degree,
-//           spread evenly over every warp of the grid;
+//           whose distances have not been relaxed yet): t_Req = A_L^T (t o t_Bi),
+//           fused with the re-introduction filter (t_Req < t) o t_Bi and with
+//           t = min(t, t_Req) (Section IV-C; the fusion of Section VI-B) through
+//           one 64-bit atomicMin per arc on packed[v] = key(t[v]) << 32 | pred[v];
 //   HEAVY   relax the heavy arcs of S, the vertices processed in bucket i:
 //           t_Req = A_H^T (t o S) (Section III-D, Fig. 1);
 //   SELECT  the next non-empty bucket: i = bucket(min key of the far pile),
-//           then the far pile is compacted into the new frontier (Fig. 1's
-//           outer loop; empty buckets are skipped).
-// A vertex whose distance strictly decreases is appended, once, to the next
-// frontier when its new bucket is <= i, otherwise to the far pile. S is
-// deduplicated with a per-bucket stamp. The phase order is decided by one
-// thread in the serial step of the grid barrier.
+//           then the far pile is compacted into F and S (Fig. 1's outer loop;
+//           empty buckets are skipped).
+// A vertex whose distance strictly decreases into bucket <= i is queued once
+// per round: its light segment goes to the next F and, once per bucket, its
+// heavy segment to S (S = S u t_Bi, Fig. 1). A decrease into a later bucket
+// puts it on the far pile.
+//
+// Load balance: F and S entries carry their arc offset within the list, so a
+// phase splits the list's flattened arcs into equal contiguous slices, one per
+// warp (merge-path). Each warp finds its first entry with a 32-ary search and
+// walks a 32-entry window of the list; every 32-arc step maps arcs to owners
+// with one scatter and a prefix-max. A hub's arcs are thus spread over the
+// whole grid and a phase costs (its arcs) / (all warps).
 //
 // DSSSP_MODE_PERSISTENT runs all phases in one cooperative launch; every
 // barrier wait is bounded by timeout_ns and ends the kernel with
 // DSSSP_ERR_TIMEOUT instead of hanging. DSSSP_MODE_STEPPED launches one kernel
-// per phase and runs the serial step as a 1-thread kernel (for profiling).
+// per phase and runs the serial step as a 1-thread kernel.
 #include "dsssp_internal.cuh"
 
 namespace dsssp {
@@ -48,7 +53,7 @@ __device__ __forceinline__ uint64_t globaltimer() {
 template <typename T>
 __device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; }
 
-// Warp-aggregated append: one atomicAdd per warp, lanes write at base + rank.
+// Warp-aggregated append of a vertex id: one atomicAdd per warp.
 // Every lane of the warp must call it.
 __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *list, uint32_t *counter) {
     const uint32_t mask = __ballot_sync(FULL, pred);
@@ -58,6 +63,31 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *l
     if ((int)lane_id() == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
     base = __shfl_sync(FULL, base, leader);
     if (pred) list[base + __popc(mask & lanemask_lt())] = val;
+}
+
+// Warp-aggregated append of (vertex, segment) to an F or S list: one 64-bit
+// atomicAdd of (entries << 32 | arcs) per warp gives both the positions and the
+// exclusive arc offsets. Every lane of the warp must call it.
+__device__ __forceinline__ void warp_push_seg(bool pred, uint32_t v, uint32_t deg, uint32_t beg, uint4 *list,
+                                              unsigned long long *ctr) {
+    const uint32_t mask = __ballot_sync(FULL, pred);
+    if (mask == 0u) return;
+    const uint32_t lane = lane_id();
+    const uint32_t d = pred ? deg : 0u;
+    uint32_t incl = d;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    const uint32_t tot = __shfl_sync(FULL, incl, 31);
+    const int leader = __ffs(mask) - 1;
+    unsigned long long old = 0;
+    if ((int)lane == leader) old = atomicAdd(ctr, ((unsigned long long)__popc(mask) << 32) | tot);
+    old = __shfl_sync(FULL, old, leader);
+    if (pred)
+        list[(uint32_t)(old >> 32) + __popc(mask & lanemask_lt())] =
+            make_uint4(v, (uint32_t)old + incl - d, beg, 0u);
 }
 
 // d (+) w on keys: float32 add rounded to nearest (+inf on overflow), or int32
@@ -79,7 +109,11 @@ __device__ __forceinline__ constexpr uint32_t inf_key() {
 
 // Per-phase constants every block reads from the control block after a barrier.
 struct Desc {
-    uint32_t mode, big_kind, cur, far_cur, qstamp, sround, T, count, count2;
+    uint32_t mode, cur, scur, far_cur, qstamp, sround, T;
+    uint32_t spush;       // S list receiving pushes in this phase
+    uint32_t sstamp;      // S stamp of those pushes
+    uint32_t count;       // entries of the list this phase reads
+    uint32_t arcs;        // arcs of that list (LIGHT / HEAVY)
 };
 
 // Block-local accumulators flushed to the control block.
@@ -88,15 +122,34 @@ struct BlockAcc {
     unsigned long long arcs_light, arcs_heavy, improvements, far_scanned;
 };
 
-// relax(v, new_dist) of Section III-C on the packed word. Returns through
-// push_near / push_far whether v must be appended to the next frontier or to
-// the far pile.
+// Pending pushes of one lane in one step.
+struct Push {
+    bool f, s, far;
+    uint32_t fdeg, fbeg, sdeg, sbeg;
+};
+
+// Queue v for bucket i (its key is now below T): once per round into the next
+// F (its light segment), once per bucket into S (its heavy segment). A live
+// far-pile entry of v becomes stale.
+__device__ __forceinline__ void queue_near(const SolveArgs &a, const Desc &d, uint32_t v, Push &p, bool mark_far) {
+    if (atomicExch(a.near_stamp + v, d.qstamp) == d.qstamp) return;
+    const uint4 vi = a.vinfo[v];
+    p.fdeg = vi.y - vi.x;
+    p.fbeg = vi.x;
+    p.f = p.fdeg != 0u;
+    if (__ldcg(a.s_stamp + v) != d.sstamp) {
+        a.s_stamp[v] = d.sstamp;
+        p.sdeg = vi.z - vi.y;
+        p.sbeg = vi.y;
+        p.s = p.sdeg != 0u;
+    }
+    if (mark_far && __ldcg(a.far_flag + v) == 1u) a.far_flag[v] = 2u;
+}
+
+// relax(v, new_dist) of Section III-C on the packed word.
 template <int DT>
 __device__ __forceinline__ void relax_arc(const SolveArgs &a, const Desc &d, uint32_t v, uint32_t ckey,
-                                          uint32_t u, bool &push_near, bool &push_far, uint32_t &far_min,
-                                          uint32_t &improved) {
-    push_near = false;
-    push_far = false;
+                                          uint32_t u, Push &p, uint32_t &far_min, uint32_t &improved) {
     if (ckey >= inf_key<DT>()) return;
     const unsigned long long cand = ((unsigned long long)ckey << 32) | u;
     // packed[v] only decreases, so any earlier value is an upper bound: skip the
@@ -106,144 +159,108 @@ __device__ __forceinline__ void relax_arc(const SolveArgs &a, const Desc &d, uin
     if (cand >= old) return;
     if ((uint32_t)(old >> 32) <= ckey) return;         // equal distance: predecessor tie-break only
     ++improved;
-    if (ckey < d.T) {                                  // new bucket <= i: (t_Req < t) o t_Bi
-        push_near = atomicExch(a.near_stamp + v, d.qstamp) != d.qstamp;
+    if (ckey < d.T) {                                  // (t_Req < t) o t_Bi: back into bucket i
+        queue_near(a, d, v, p, true);
     } else {                                           // a later bucket: far pile
         far_min = min(far_min, ckey);
-        push_far = atomicExch(a.far_flag + v, 1u) == 0u;
+        p.far = atomicExch(a.far_flag + v, 1u) == 0u;
     }
 }
 
-// LIGHT / HEAVY: every warp takes batches of 32 list entries (static round
-// robin), expands their arc segments cooperatively (exclusive scan of the
-// segment lengths, then 32 arcs per step), and relaxes each arc. Segments
-// longer than big_degree go to the BIG list instead.
+__device__ __forceinline__ void flush_pushes(const SolveArgs &a, const Desc &d, const Push &p, uint32_t v) {
+    Ctl *c = a.ctl;
+    warp_push_seg(p.f, v, p.fdeg, p.fbeg, d.cur ? a.F0 : a.F1, &c->ctrF[d.cur ^ 1u]);
+    warp_push_seg(p.s, v, p.sdeg, p.sbeg, d.spush ? a.S1 : a.S0, &c->ctrS[d.spush]);
+    warp_append(p.far, v, d.far_cur ? a.FAR1 : a.FAR0, &c->nFar[d.far_cur]);
+}
+
+// LIGHT / HEAVY: relax the arcs of a list, split evenly over all warps.
 template <int DT, bool LIGHT>
-__device__ void phase_segments(const SolveArgs &a, const Desc &d, BlockAcc &acc, uint32_t *sw) {
+__device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot) {
     const uint32_t lane = lane_id();
-    const uint32_t wib = threadIdx.x >> 5;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    uint32_t *sw_scan = sw + wib * 128;
-    uint32_t *sw_beg = sw_scan + 32;
-    uint32_t *sw_key = sw_scan + 64;
-    uint32_t *sw_u = sw_scan + 96;
-    Ctl *c = a.ctl;
-    const uint32_t *list = LIGHT ? (d.cur ? a.F1 : a.F0) : a.S;
+    const uint4 *list = LIGHT ? (d.cur ? a.F1 : a.F0) : (d.scur ? a.S1 : a.S0);
+    const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[4 * j]
     const uint32_t count = d.count;
-    uint32_t *next = d.cur ? a.F0 : a.F1;
-    uint32_t *next_cnt = &c->nF[d.cur ^ 1u];
-    uint32_t *farl = d.far_cur ? a.FAR1 : a.FAR0;
-    uint32_t *far_cnt = &c->nFar[d.far_cur];
-    uint32_t far_min = inf_key<DT>();
-    uint32_t improved = 0;
-    unsigned long long arcs = 0;
-
-    for (uint32_t batch = gw; (unsigned long long)batch * 32u < count; batch += nw) {
-        const uint32_t idx = batch * 32u + lane;
-        const bool valid = idx < count;
-        uint32_t u = 0, beg = 0, deg = 0, dkey = inf_key<DT>();
-        bool addS = false;
-        if (valid) {
-            u = __ldcg(list + idx);
-            dkey = (uint32_t)(__ldcg(a.packed + u) >> 32);
-            const uint4 vi = a.vinfo[u];
-            if (LIGHT) {
-                beg = vi.x;
-                deg = vi.y - vi.x;
-                addS = __ldcg(a.s_stamp + u) != d.sround;      // S = S u B_i
-                if (addS) a.s_stamp[u] = d.sround;
-                if (__ldcg(a.far_flag + u) == 1u) a.far_flag[u] = 2u;   // its far entry is now stale
-            } else {
-                beg = vi.y;
-                deg = vi.z - vi.y;
-            }
-            if (deg > a.big_degree) {
-                const unsigned long long old =
-                    atomicAdd(&c->big_ctr, (1ull << 32) | (unsigned long long)deg);
-                a.BIG[(uint32_t)(old >> 32)] = make_uint4(u, (uint32_t)old, beg, 0u);
-                deg = 0;
-            }
-        }
-        if (LIGHT) warp_append(addS, u, a.S, &c->nS);
-
-        uint32_t incl = deg;
-        #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, incl, o);
-            if ((int)lane >= o) incl += t;
-        }
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        sw_scan[lane] = incl - deg;
-        sw_beg[lane] = beg;
-        sw_key[lane] = dkey;
-        sw_u[lane] = u;
-        __syncwarp();
-        arcs += total;
-        uint32_t j = 0;
-        for (uint32_t base = 0; base < total; base += 32u) {
-            const uint32_t e = base + lane;
-            bool pn = false, pf = false;
-            uint32_t v = 0;
-            if (e < total) {
-                while (j < 31u && sw_scan[j + 1] <= e) ++j;
-                const uint2 arc = a.arcs[sw_beg[j] + (e - sw_scan[j])];
-                v = arc.x;
-                relax_arc<DT>(a, d, v, key_add<DT>(sw_key[j], arc.y), sw_u[j], pn, pf, far_min, improved);
-            }
-            warp_append(pn, v, next, next_cnt);
-            warp_append(pf, v, farl, far_cnt);
-        }
-        __syncwarp();
-    }
-    if (lane == 0 && arcs) {
-        if (LIGHT) atomicAdd(&acc.arcs_light, arcs); else atomicAdd(&acc.arcs_heavy, arcs);
-    }
-    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
-    if (improved) atomicAdd(&acc.improvements, (unsigned long long)improved);
-}
-
-// BIG: the flattened arcs of the long segments, split evenly over all warps.
-template <int DT>
-__device__ void phase_big(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
-    const uint32_t lane = lane_id();
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t nb = d.count;        // entries
-    const uint32_t E = d.count2;        // arcs
-    Ctl *c = a.ctl;
-    uint32_t *next = d.cur ? a.F0 : a.F1;
-    uint32_t *next_cnt = &c->nF[d.cur ^ 1u];
-    uint32_t *farl = d.far_cur ? a.FAR1 : a.FAR0;
-    uint32_t *far_cnt = &c->nFar[d.far_cur];
-    uint32_t far_min = inf_key<DT>();
-    uint32_t improved = 0;
+    const uint32_t E = d.arcs;
     const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
     const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
+    uint32_t far_min = inf_key<DT>();
+    uint32_t improved = 0;
     if (e0 < e1) {
-        // owner of e0: the last entry whose offset is <= e0
-        uint32_t lo = 0, hi = nb - 1;
-        while (lo < hi) {
-            const uint32_t mid = (lo + hi + 1) >> 1;
-            if (__ldcg(&a.BIG[mid].y) <= e0) lo = mid; else hi = mid - 1;
+        // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
+        uint32_t lo = 0, hi = count;
+        while (hi - lo > 32u) {
+            const uint32_t step = (hi - lo + 31u) >> 5;
+            const uint32_t p = lo + lane * step;
+            const bool ok = p < hi && __ldcg(offs + 4ull * p) <= e0;
+            const uint32_t k = 31u - __clz(__ballot_sync(FULL, ok));
+            lo += k * step;
+            hi = min(hi, lo + step);
         }
-        uint32_t j0 = lo;
-        for (uint32_t base = e0; base < e1; base += 32u) {
-            const uint32_t e = base + lane;
-            uint32_t j = j0;
-            bool pn = false, pf = false;
-            uint32_t v = 0;
-            if (e < e1) {
-                while (j + 1 < nb && __ldcg(&a.BIG[j + 1].y) <= e) ++j;
-                const uint4 b = __ldcg(a.BIG + j);
-                const uint32_t dkey = (uint32_t)(__ldcg(a.packed + b.x) >> 32);
-                const uint2 arc = a.arcs[b.z + (e - b.y)];
-                v = arc.x;
-                relax_arc<DT>(a, d, v, key_add<DT>(dkey, arc.y), b.x, pn, pf, far_min, improved);
+        {
+            const uint32_t p = lo + lane;
+            const bool ok = p < hi && __ldcg(offs + 4ull * p) <= e0;
+            lo += 31u - __clz(__ballot_sync(FULL, ok));
+        }
+        // window: lane k holds entry jw + k; wend = arc offset just past the window
+        uint32_t jw = lo, wv = 0, woff = 0xFFFFFFFFu, wbeg = 0, wkey = inf_key<DT>(), wend = 0;
+        auto load_window = [&](uint32_t j) {
+            const uint32_t idx = j + lane;
+            if (idx < count) {
+                const uint4 en = __ldcg(list + idx);
+                wv = en.x < a.n ? en.x : 0u;          // defensive: ids come from device lists
+                woff = en.y;
+                wbeg = en.z;
+                wkey = (uint32_t)(__ldcg(a.packed + wv) >> 32);
+            } else {
+                wv = 0; woff = 0xFFFFFFFFu; wbeg = 0; wkey = inf_key<DT>();
             }
-            warp_append(pn, v, next, next_cnt);
-            warp_append(pf, v, farl, far_cnt);
-            j0 = __shfl_sync(FULL, j, 31);
+            wend = (j + 32u < count) ? __ldcg(offs + 4ull * (j + 32u)) : E;
+        };
+        load_window(jw);
+        int *sl = slot + (threadIdx.x >> 5) * 32;
+        for (uint32_t base = e0; base < e1; base += 32u) {
+            const uint32_t last = min(base + 31u, e1 - 1u);
+            if (last >= wend) {
+                // move the window to the owner of `base` (inside it, or the entry just past it)
+                const uint32_t shift = base >= wend ? 32u : 31u - __clz(__ballot_sync(FULL, woff <= base));
+                jw += shift;
+                load_window(jw);
+            }
+            // owner of arc base + lane: the last window entry starting at or before it
+            const int carry = 31 - __clz(__ballot_sync(FULL, woff <= base));
+            sl[lane] = -1;
+            __syncwarp();
+            if (woff > base && woff - base < 32u) sl[woff - base] = (int)lane;
+            __syncwarp();
+            int own = sl[lane];
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(FULL, own, o);
+                if ((int)lane >= o) own = max(own, t);
+            }
+            own = max(own, carry);
+            __syncwarp();
+            const uint32_t ov = __shfl_sync(FULL, wv, own);
+            const uint32_t ooff = __shfl_sync(FULL, woff, own);
+            const uint32_t obeg = __shfl_sync(FULL, wbeg, own);
+            const uint32_t okey = __shfl_sync(FULL, wkey, own);
+            const uint32_t e = base + lane;
+            Push p{};
+            uint32_t v = 0;
+            const uint32_t ai = obeg + (e - ooff);
+            if (e < e1 && ai < a.m) {                 // defensive bound; always true when lists are consistent
+                const uint2 arc = a.arcs[ai];
+                v = arc.x;
+                relax_arc<DT>(a, d, v, key_add<DT>(okey, arc.y), ov, p, far_min, improved);
+            }
+            flush_pushes(a, d, p, v);
+        }
+        if (lane == 0) {
+            if (LIGHT) atomicAdd(&acc.arcs_light, (unsigned long long)(e1 - e0));
+            else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
         }
     }
     if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
@@ -251,8 +268,8 @@ __device__ void phase_big(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
 }
 
 // SELECT: compact the far pile. Live entries whose key is below T (bucket <= i)
-// move to the frontier; the rest stay, and their minimum key bounds the next
-// bucket; stale entries are dropped.
+// are queued into F and S; the rest stay, and their minimum key bounds the
+// next bucket; stale entries are dropped.
 template <int DT>
 __device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
     const uint32_t lane = lane_id();
@@ -262,21 +279,19 @@ __device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
     const uint32_t *in = d.far_cur ? a.FAR1 : a.FAR0;
     uint32_t *out = d.far_cur ? a.FAR0 : a.FAR1;
     uint32_t *out_cnt = &c->nFar[d.far_cur ^ 1u];
-    uint32_t *next = d.cur ? a.F0 : a.F1;
-    uint32_t *next_cnt = &c->nF[d.cur ^ 1u];
     uint32_t far_min = inf_key<DT>();
     const uint32_t count = d.count;
     for (unsigned long long base = (unsigned long long)gw * 32u; base < count; base += (unsigned long long)nw * 32u) {
         const uint32_t idx = (uint32_t)base + lane;
-        bool take = false, keep = false;
+        Push p{};
+        bool keep = false;
         uint32_t v = 0;
-        if (idx < count) {
-            v = __ldcg(in + idx);
+        if (idx < count && (v = __ldcg(in + idx)) < a.n) {
             if (__ldcg(a.far_flag + v) == 1u) {
                 const uint32_t k = (uint32_t)(__ldcg(a.packed + v) >> 32);
                 if (k < d.T) {
                     a.far_flag[v] = 0u;
-                    take = atomicExch(a.near_stamp + v, d.qstamp) != d.qstamp;
+                    queue_near(a, d, v, p, false);
                 } else {
                     keep = true;
                     far_min = min(far_min, k);
@@ -285,7 +300,8 @@ __device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
                 a.far_flag[v] = 0u;
             }
         }
-        warp_append(take, v, next, next_cnt);
+        warp_push_seg(p.f, v, p.fdeg, p.fbeg, d.cur ? a.F0 : a.F1, &c->ctrF[d.cur ^ 1u]);
+        warp_push_seg(p.s, v, p.sdeg, p.sbeg, d.spush ? a.S1 : a.S0, &c->ctrS[d.spush]);
         warp_append(keep, v, out, out_cnt);
     }
     if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
@@ -302,8 +318,8 @@ __device__ void serial_step(const SolveArgs &a) {
     const uint64_t dt = now - c->t_last;
     c->t_last = now;
     const uint32_t mode = c->mode;
-    if (mode == MODE_LIGHT || (mode == MODE_BIG && c->big_kind == 0u)) c->st[ST_NSLIGHT] += (long long)dt;
-    else if (mode == MODE_HEAVY || mode == MODE_BIG) c->st[ST_NSHEAVY] += (long long)dt;
+    if (mode == MODE_LIGHT) c->st[ST_NSLIGHT] += (long long)dt;
+    else if (mode == MODE_HEAVY) c->st[ST_NSHEAVY] += (long long)dt;
     else if (mode == MODE_SELECT) c->st[ST_NSSELECT] += (long long)dt;
     c->phases += 1;
     if (c->phases >= a.max_phases) {
@@ -311,50 +327,38 @@ __device__ void serial_step(const SolveArgs &a) {
         c->mode = MODE_DONE;
         return;
     }
-    const uint32_t nxt = c->cur ^ 1u;
-    int next;   // 0: after light, 1: after heavy, 2: select
     switch (mode) {
     case MODE_LIGHT:
         c->st[ST_LIGHT] += 1;
-        c->st[ST_VLIGHT] += c->nF[c->cur];
-        c->nF[c->cur] = 0;
-        if ((c->big_ctr >> 32) != 0ull) { c->mode = MODE_BIG; c->big_kind = 0u; return; }
-        next = 0;
-        break;
-    case MODE_BIG:
-        c->st[ST_BIGP] += 1;
-        c->big_ctr = 0ull;
-        next = c->big_kind == 0u ? 0 : 1;
+        c->st[ST_VLIGHT] += (long long)(c->ctrF[c->cur] >> 32);
+        c->ctrF[c->cur] = 0ull;
         break;
     case MODE_HEAVY:
         c->st[ST_HEAVY] += 1;
-        c->st[ST_VHEAVY] += c->nS;
-        c->nS = 0;
+        c->st[ST_VHEAVY] += (long long)(c->ctrS[c->scur] >> 32);
+        c->ctrS[c->scur] = 0ull;
+        c->scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
         c->sround += 1u;
-        if ((c->big_ctr >> 32) != 0ull) { c->mode = MODE_BIG; c->big_kind = 1u; return; }
-        next = 1;
         break;
     case MODE_SELECT:
         c->st[ST_SELECT] += 1;
-        c->nFar[c->far_cur] = 0;
+        c->nFar[c->far_cur] = 0u;
         c->far_cur ^= 1u;
-        if (c->nF[nxt] != 0u) {                 // bucket i has vertices: light rounds
-            c->st[ST_BUCKETS] += 1;
-            c->cur = nxt; c->qstamp += 1u; c->mode = MODE_LIGHT;
-            return;
-        }
-        next = 2;
         break;
     default:
         return;
     }
-    if (next == 0) {                            // inner loop of Fig. 1: while t_Bi != 0
-        if (c->nF[nxt] != 0u) { c->cur = nxt; c->qstamp += 1u; c->mode = MODE_LIGHT; }
-        else c->mode = MODE_HEAVY;
+    c->qstamp += 1u;                           // every phase queues under a fresh stamp
+    const uint32_t nxt = c->cur ^ 1u;
+    if ((c->ctrF[nxt] >> 32) != 0ull) {        // inner loop of Fig. 1: while t_Bi != 0
+        if (mode == MODE_SELECT) c->st[ST_BUCKETS] += 1;
+        c->cur = nxt;
+        c->mode = MODE_LIGHT;
         return;
     }
-    if (next == 1 && c->nF[nxt] != 0u) {        // a rounded heavy sum re-opened bucket i
-        c->cur = nxt; c->qstamp += 1u; c->mode = MODE_LIGHT;
+    if ((c->ctrS[c->scur] >> 32) != 0ull) {    // bucket settled: heavy pass over S
+        if (mode == MODE_SELECT) c->st[ST_BUCKETS] += 1;
+        c->mode = MODE_HEAVY;
         return;
     }
     // next non-empty bucket
@@ -378,29 +382,30 @@ __device__ void serial_step(const SolveArgs &a) {
 
 __device__ __forceinline__ void read_desc(const Ctl *c, Desc &d) {
     d.mode = vload(&c->mode);
-    d.big_kind = vload(&c->big_kind);
     d.cur = vload(&c->cur);
+    d.scur = vload(&c->scur);
     d.far_cur = vload(&c->far_cur);
     d.qstamp = vload(&c->qstamp);
     d.sround = vload(&c->sround);
     d.T = vload(&c->T);
+    // S pushes: into the current S, except during a heavy pass, which feeds the next one
+    d.spush = d.mode == MODE_HEAVY ? d.scur ^ 1u : d.scur;
+    d.sstamp = d.mode == MODE_HEAVY ? d.sround + 1u : d.sround;
     d.count = 0;
-    d.count2 = 0;
+    d.arcs = 0;
+    unsigned long long ctr = 0;
     switch (d.mode) {
-    case MODE_LIGHT: d.count = vload(&c->nF[d.cur]); break;
-    case MODE_HEAVY: d.count = vload(&c->nS); break;
+    case MODE_LIGHT: ctr = vload(&c->ctrF[d.cur]); break;
+    case MODE_HEAVY: ctr = vload(&c->ctrS[d.scur]); break;
     case MODE_SELECT: d.count = vload(&c->nFar[d.far_cur]); break;
-    case MODE_BIG: {
-        const unsigned long long b = vload(&c->big_ctr);
-        d.count = (uint32_t)(b >> 32);
-        d.count2 = (uint32_t)b;
-        break;
-    }
     default: break;
+    }
+    if (d.mode == MODE_LIGHT || d.mode == MODE_HEAVY) {
+        d.count = (uint32_t)(ctr >> 32);
+        d.arcs = (uint32_t)ctr;
     }
 }
 
-// Flush the block's far-pile minimum before arriving at a barrier.
 __device__ __forceinline__ void flush_far_min(Ctl *c, BlockAcc &acc, uint32_t inf) {
     if (acc.far_min < inf) {
         atomicMin(&c->far_min, acc.far_min);
@@ -417,7 +422,7 @@ __device__ __forceinline__ void flush_stats(Ctl *c, BlockAcc &acc) {
 }
 
 // Grid-wide barrier with a serial step, every wait bounded by timeout_ns.
-// Returns false when the solve must stop (error recorded, or timed out).
+// Returns false when the solve must stop (done, error recorded, or timed out).
 template <int DT>
 __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
     __syncthreads();
@@ -435,15 +440,12 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
             atomicExch(&c->bar_gen, gen + 1u);
         } else {
             const uint64_t t0 = globaltimer();
-            unsigned sleep_ns = 32;
             while (vload(&c->bar_gen) == gen) {
                 if (vload(&c->err) != 0) break;
                 if ((int64_t)(globaltimer() - t0) > a.timeout_ns) {
                     atomicCAS(&c->err, 0, (int)DSSSP_ERR_TIMEOUT);
                     break;
                 }
-                __nanosleep(sleep_ns);
-                if (sleep_ns < 256) sleep_ns <<= 1;
             }
             __threadfence();
         }
@@ -454,11 +456,10 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
 }
 
 template <int DT>
-__device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, BlockAcc &acc, uint32_t *sw) {
+__device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot) {
     switch (d.mode) {
-    case MODE_LIGHT: phase_segments<DT, true>(a, d, acc, sw); break;
-    case MODE_HEAVY: phase_segments<DT, false>(a, d, acc, sw); break;
-    case MODE_BIG: phase_big<DT>(a, d, acc); break;
+    case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot); break;
+    case MODE_HEAVY: phase_arcs<DT, false>(a, d, acc, slot); break;
     case MODE_SELECT: phase_select<DT>(a, d, acc); break;
     default: break;
     }
@@ -466,7 +467,7 @@ __device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, Blo
 
 template <int DT>
 __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
-    __shared__ uint32_t sw[kMaxWarps * 128];
+    __shared__ int slot[kMaxWarps * 32];
     __shared__ Desc s_desc;
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
@@ -480,7 +481,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
         __syncthreads();
         const Desc d = s_desc;
         if (d.mode == MODE_DONE) break;
-        run_phase<DT>(a, d, acc, sw);
+        run_phase<DT>(a, d, acc, slot);
         if (!grid_barrier<DT>(a, acc, &s_ok)) break;
     }
     __syncthreads();
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
 // ---- stepped mode: one launch per phase --------------------------------------
 template <int DT, uint32_t MODE>
 __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
-    __shared__ uint32_t sw[kMaxWarps * 128];
+    __shared__ int slot[kMaxWarps * 32];
     __shared__ Desc s_desc;
     __shared__ BlockAcc acc;
     if (threadIdx.x == 0) {
@@ -501,7 +502,7 @@ __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __syncthreads();
     const Desc d = s_desc;
     if (d.mode != MODE) return;
-    run_phase<DT>(a, d, acc, sw);
+    run_phase<DT>(a, d, acc, slot);
     __syncthreads();
     if (threadIdx.x == 0) {
         flush_far_min(a.ctl, acc, inf_key<DT>());
@@ -520,36 +521,38 @@ __global__ void k_init(SolveArgs a) {
     const uint32_t n = a.n;
     const unsigned long long unreached = ((unsigned long long)inf_key<DT>() << 32) | NO_PRED;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        // t = inf, t[s] = 0 (Fig. 1); predecessor of s is s
+        // t = inf, t[s] = 0 (Fig. 1); the predecessor of s is s
         a.packed[v] = v == a.src ? (unsigned long long)a.src : unreached;
-        a.near_stamp[v] = 0u;
+        a.near_stamp[v] = v == a.src ? 1u : 0u;
         a.far_flag[v] = 0u;
-        a.s_stamp[v] = 0u;
+        a.s_stamp[v] = v == a.src ? 1u : 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctl *c = a.ctl;
+        const uint4 vs = a.vinfo[a.src];
         c->bar_count = 0u;
         c->bar_gen = 0u;
         c->mode = MODE_LIGHT;     // B_0 = {s}
-        c->big_kind = 0u;
         c->cur = 0u;
+        c->scur = 0u;
         c->far_cur = 0u;
         c->qstamp = 1u;
         c->sround = 1u;
         c->bucket = 0;
         c->T = bucket_floor_key(1, DT, a.delta);
-        c->nF[0] = 1u;
-        c->nF[1] = 0u;
-        c->nS = 0u;
+        c->ctrF[0] = (vs.y > vs.x) ? ((1ull << 32) | (vs.y - vs.x)) : 0ull;
+        c->ctrF[1] = 0ull;
+        c->ctrS[0] = (vs.z > vs.y) ? ((1ull << 32) | (vs.z - vs.y)) : 0ull;
+        c->ctrS[1] = 0ull;
         c->nFar[0] = c->nFar[1] = 0u;
         c->far_min = inf_key<DT>();
-        c->big_ctr = 0ull;
         c->err = 0;
         c->phases = 0;
         for (int k = 0; k < 16; ++k) c->st[k] = 0;
         c->st[ST_BUCKETS] = 1;
         c->t_start = c->t_last = globaltimer();
-        a.F0[0] = a.src;
+        a.F0[0] = make_uint4(a.src, 0u, vs.x, 0u);
+        a.S0[0] = make_uint4(a.src, 0u, vs.y, 0u);
     }
 }
 
@@ -600,7 +603,6 @@ cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, in
         break;
     switch (mode) {
         DSSSP_PHASE_CASE(MODE_LIGHT)
-        DSSSP_PHASE_CASE(MODE_BIG)
         DSSSP_PHASE_CASE(MODE_HEAVY)
         DSSSP_PHASE_CASE(MODE_SELECT)
     default: break;

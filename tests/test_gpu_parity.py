@@ -50,7 +50,7 @@ def assert_same(g, src, d, p, d_ref=None, p_ref=None, what=""):
     assert badp.size == 0, f"{what}: {badp.size} predecessors differ, first {badp[:5]} gpu {p[badp[:5]]} ref {p_ref[badp[:5]]}"
 
 
-MODES = [dict(), dict(mode=1), dict(big_degree=32, grid_size=3)]
+MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64)]
 
 
 # ------------------------------------------------------------------ hand-built cases
@@ -108,7 +108,7 @@ def test_edge_cases(ds):
                                      dtype=np.float32), 0))
     cases.append((graphgen.from_arcs(3, [(0, 1), (0, 2), (1, 2)], np.array([-0.0, 1.0, 0.0], np.float32),
                                      dtype=np.float32), 0))
-    # a hub whose out-degree exceeds big_degree, zero-weight arcs into the source
+    # a hub whose arcs span many warps' slices, zero-weight arcs into the source
     k = 5000
     rng = np.random.default_rng(3)
     hub_w = rng.integers(0, 50, k).astype(np.int32)
@@ -137,7 +137,7 @@ def test_rmat14_int_delta32(ds):
     g, srcs, deltas = W.rmat14_int()
     h = ds.Graph(g.row_ptr, g.col, g.w)
     d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, srcs[0])
-    for opt in MODES + [dict(grid_size=1), dict(block_size=128), dict(big_degree=64)]:
+    for opt in MODES + [dict(grid_size=1), dict(block_size=128), dict(grid_size=7, block_size=32)]:
         d, p, st = gpu_solve(ds, h, srcs[0], deltas[0], **opt)
         assert_same(g, srcs[0], d, p, d_ref, p_ref, str(opt))
         assert st["buckets"] >= 1 and st["arcs_light"] > 0
