@@ -275,7 +275,14 @@ def main():
                 "phases": sum(st["light_phases"] + st["heavy_phases"] + st["select_phases"]
                               for st in stats[d]) / len(srcs),
                 "arcs_relaxed_per_solve": sum(st["arcs_light"] + st["arcs_heavy"] for st in stats[d]) / len(srcs),
-                "kernel_us_per_solve": sum(st["ns_total"] for st in stats[d]) / len(srcs) / 1e3})
+                "kernel_us_per_solve": sum(st["ns_total"] for st in stats[d]) / len(srcs) / 1e3,
+                "us_light": sum(st["ns_light"] for st in stats[d]) / len(srcs) / 1e3,
+                "us_heavy": sum(st["ns_heavy"] for st in stats[d]) / len(srcs) / 1e3,
+                "us_select": sum(st["ns_select"] for st in stats[d]) / len(srcs) / 1e3,
+                "light_phases": sum(st["light_phases"] for st in stats[d]) / len(srcs),
+                "arcs_light": sum(st["arcs_light"] for st in stats[d]) / len(srcs),
+                "improvements": sum(st["improvements"] for st in stats[d]) / len(srcs),
+                "far_scanned": sum(st["far_scanned"] for st in stats[d]) / len(srcs)})
         peak, peak_kind = measured_peak_gbs()
         achieved = tot_bytes / (tot_ms * 1e-3) / 1e9
         light_gbs = tot_light_b / (tot_light_ns * 1e-9) / 1e9 if tot_light_ns else None

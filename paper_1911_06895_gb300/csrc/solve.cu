@@ -53,27 +53,21 @@ __device__ __forceinline__ uint64_t globaltimer() {
 template <typename T>
 __device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; }
 
-// Warp-aggregated append of a vertex id: one atomicAdd per warp.
-// Every lane of the warp must call it.
-__device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *list, uint32_t *counter) {
-    const uint32_t mask = __ballot_sync(FULL, pred);
-    if (mask == 0u) return;
-    const int leader = __ffs(mask) - 1;
-    uint32_t base = 0;
-    if ((int)lane_id() == leader) base = atomicAdd(counter, (uint32_t)__popc(mask));
-    base = __shfl_sync(FULL, base, leader);
-    if (pred) list[base + __popc(mask & lanemask_lt())] = val;
-}
+// Per-warp staging of pushes in shared memory. A list counter is touched once
+// per 32 staged entries instead of once per 32-arc step, which removes the
+// serialization of many warps' atomics on the same three counters.
+struct WarpStage {
+    uint32_t fv[64], fd[64], fb[64];     // next-frontier entries (vertex, light degree, begin)
+    uint32_t sv[64], sd[64], sb[64];     // S entries (vertex, heavy degree, begin)
+    uint32_t far[64];                    // far-pile entries
+};
 
-// Warp-aggregated append of (vertex, segment) to an F or S list: one 64-bit
-// atomicAdd of (entries << 32 | arcs) per warp gives both the positions and the
-// exclusive arc offsets. Every lane of the warp must call it.
-__device__ __forceinline__ void warp_push_seg(bool pred, uint32_t v, uint32_t deg, uint32_t beg, uint4 *list,
-                                              unsigned long long *ctr) {
-    const uint32_t mask = __ballot_sync(FULL, pred);
-    if (mask == 0u) return;
+// Write n <= 32 staged segment entries (lanes < n) to an F or S list.
+__device__ __forceinline__ void flush_seg(const uint32_t *bv, const uint32_t *bd, const uint32_t *bb, uint32_t n,
+                                          uint4 *list, unsigned long long *ctr) {
     const uint32_t lane = lane_id();
-    const uint32_t d = pred ? deg : 0u;
+    const bool has = lane < n;
+    const uint32_t v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u, b = has ? bb[lane] : 0u;
     uint32_t incl = d;
     #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -81,13 +75,63 @@ __device__ __forceinline__ void warp_push_seg(bool pred, uint32_t v, uint32_t de
         if ((int)lane >= o) incl += t;
     }
     const uint32_t tot = __shfl_sync(FULL, incl, 31);
-    const int leader = __ffs(mask) - 1;
     unsigned long long old = 0;
-    if ((int)lane == leader) old = atomicAdd(ctr, ((unsigned long long)__popc(mask) << 32) | tot);
-    old = __shfl_sync(FULL, old, leader);
-    if (pred)
-        list[(uint32_t)(old >> 32) + __popc(mask & lanemask_lt())] =
-            make_uint4(v, (uint32_t)old + incl - d, beg, 0u);
+    if (lane == 0) old = atomicAdd(ctr, ((unsigned long long)n << 32) | tot);
+    old = __shfl_sync(FULL, old, 0);
+    if (has) list[(uint32_t)(old >> 32) + lane] = make_uint4(v, (uint32_t)old + incl - d, b, 0u);
+}
+
+__device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32_t *list, uint32_t *counter) {
+    const uint32_t lane = lane_id();
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(counter, n);
+    base = __shfl_sync(FULL, base, 0);
+    if (lane < n) list[base + lane] = bv[lane];
+}
+
+// Stage one (vertex, degree, begin) per pushing lane; flush 32 when full.
+__device__ __forceinline__ void stage_seg(bool pred, uint32_t v, uint32_t deg, uint32_t beg, uint32_t *bv,
+                                          uint32_t *bd, uint32_t *bb, uint32_t &cnt, uint4 *list,
+                                          unsigned long long *ctr) {
+    const uint32_t mask = __ballot_sync(FULL, pred);
+    if (mask == 0u) return;
+    const uint32_t lane = lane_id();
+    if (pred) {
+        const uint32_t k = cnt + __popc(mask & lanemask_lt());
+        bv[k] = v; bd[k] = deg; bb[k] = beg;
+    }
+    cnt += __popc(mask);
+    __syncwarp();
+    if (cnt >= 32u) {
+        flush_seg(bv, bd, bb, 32u, list, ctr);
+        const uint32_t rest = cnt - 32u;
+        uint32_t x = 0, y = 0, z = 0;
+        if (lane < rest) { x = bv[32 + lane]; y = bd[32 + lane]; z = bb[32 + lane]; }
+        __syncwarp();
+        if (lane < rest) { bv[lane] = x; bd[lane] = y; bb[lane] = z; }
+        __syncwarp();
+        cnt = rest;
+    }
+}
+
+__device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, uint32_t &cnt, uint32_t *list,
+                                         uint32_t *counter) {
+    const uint32_t mask = __ballot_sync(FULL, pred);
+    if (mask == 0u) return;
+    const uint32_t lane = lane_id();
+    if (pred) bv[cnt + __popc(mask & lanemask_lt())] = v;
+    cnt += __popc(mask);
+    __syncwarp();
+    if (cnt >= 32u) {
+        flush_ids(bv, 32u, list, counter);
+        const uint32_t rest = cnt - 32u;
+        uint32_t x = 0;
+        if (lane < rest) x = bv[32 + lane];
+        __syncwarp();
+        if (lane < rest) bv[lane] = x;
+        __syncwarp();
+        cnt = rest;
+    }
 }
 
 // d (+) w on keys: float32 add rounded to nearest (+inf on overflow), or int32
@@ -167,16 +211,48 @@ __device__ __forceinline__ void relax_arc(const SolveArgs &a, const Desc &d, uin
     }
 }
 
-__device__ __forceinline__ void flush_pushes(const SolveArgs &a, const Desc &d, const Push &p, uint32_t v) {
+// The lists a phase pushes into, and the warp's staged counts.
+struct PushCtx {
+    uint4 *F;
+    unsigned long long *ctrF;
+    uint4 *S;
+    unsigned long long *ctrS;
+    uint32_t *FAR;
+    uint32_t *nFar;
+    uint32_t nf, ns, nfar;
+};
+
+__device__ __forceinline__ PushCtx push_ctx(const SolveArgs &a, const Desc &d) {
     Ctl *c = a.ctl;
-    warp_push_seg(p.f, v, p.fdeg, p.fbeg, d.cur ? a.F0 : a.F1, &c->ctrF[d.cur ^ 1u]);
-    warp_push_seg(p.s, v, p.sdeg, p.sbeg, d.spush ? a.S1 : a.S0, &c->ctrS[d.spush]);
-    warp_append(p.far, v, d.far_cur ? a.FAR1 : a.FAR0, &c->nFar[d.far_cur]);
+    PushCtx q;
+    q.F = d.cur ? a.F0 : a.F1;
+    q.ctrF = &c->ctrF[d.cur ^ 1u];
+    q.S = d.spush ? a.S1 : a.S0;
+    q.ctrS = &c->ctrS[d.spush];
+    q.FAR = d.far_cur ? a.FAR1 : a.FAR0;
+    q.nFar = &c->nFar[d.far_cur];
+    q.nf = q.ns = q.nfar = 0u;
+    return q;
+}
+
+__device__ __forceinline__ void stage_pushes(PushCtx &q, WarpStage &ws, const Push &p, uint32_t v) {
+    stage_seg(p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
+    stage_seg(p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
+    stage_id(p.far, v, ws.far, q.nfar, q.FAR, q.nFar);
+}
+
+// Flush the partially filled staging buffers (end of a phase).
+__device__ __forceinline__ void drain_pushes(PushCtx &q, WarpStage &ws) {
+    if (q.nf) flush_seg(ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
+    if (q.ns) flush_seg(ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
+    if (q.nfar) flush_ids(ws.far, q.nfar, q.FAR, q.nFar);
+    __syncwarp();
+    q.nf = q.ns = q.nfar = 0u;
 }
 
 // LIGHT / HEAVY: relax the arcs of a list, split evenly over all warps.
 template <int DT, bool LIGHT>
-__device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot) {
+__device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot, WarpStage *stage) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -188,6 +264,8 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
     const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
     uint32_t far_min = inf_key<DT>();
     uint32_t improved = 0;
+    PushCtx q = push_ctx(a, d);
+    WarpStage &ws = stage[threadIdx.x >> 5];
     if (e0 < e1) {
         // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
         uint32_t lo = 0, hi = count;
@@ -256,8 +334,9 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
                 v = arc.x;
                 relax_arc<DT>(a, d, v, key_add<DT>(okey, arc.y), ov, p, far_min, improved);
             }
-            flush_pushes(a, d, p, v);
+            stage_pushes(q, ws, p, v);
         }
+        drain_pushes(q, ws);
         if (lane == 0) {
             if (LIGHT) atomicAdd(&acc.arcs_light, (unsigned long long)(e1 - e0));
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
@@ -271,7 +350,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
 // are queued into F and S; the rest stay, and their minimum key bounds the
 // next bucket; stale entries are dropped.
 template <int DT>
-__device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
+__device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc, WarpStage *stage) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -281,6 +360,9 @@ __device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
     uint32_t *out_cnt = &c->nFar[d.far_cur ^ 1u];
     uint32_t far_min = inf_key<DT>();
     const uint32_t count = d.count;
+    PushCtx q = push_ctx(a, d);
+    WarpStage &ws = stage[threadIdx.x >> 5];
+    uint32_t nkeep = 0;
     for (unsigned long long base = (unsigned long long)gw * 32u; base < count; base += (unsigned long long)nw * 32u) {
         const uint32_t idx = (uint32_t)base + lane;
         Push p{};
@@ -300,10 +382,12 @@ __device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc) {
                 a.far_flag[v] = 0u;
             }
         }
-        warp_push_seg(p.f, v, p.fdeg, p.fbeg, d.cur ? a.F0 : a.F1, &c->ctrF[d.cur ^ 1u]);
-        warp_push_seg(p.s, v, p.sdeg, p.sbeg, d.spush ? a.S1 : a.S0, &c->ctrS[d.spush]);
-        warp_append(keep, v, out, out_cnt);
+        stage_seg(p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
+        stage_seg(p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
+        stage_id(keep, v, ws.far, nkeep, out, out_cnt);
     }
+    drain_pushes(q, ws);
+    if (nkeep) flush_ids(ws.far, nkeep, out, out_cnt);
     if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
     if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&acc.far_scanned, (unsigned long long)count);
 }
@@ -456,11 +540,12 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
 }
 
 template <int DT>
-__device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot) {
+__device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot,
+                                          WarpStage *stage) {
     switch (d.mode) {
-    case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot); break;
-    case MODE_HEAVY: phase_arcs<DT, false>(a, d, acc, slot); break;
-    case MODE_SELECT: phase_select<DT>(a, d, acc); break;
+    case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot, stage); break;
+    case MODE_HEAVY: phase_arcs<DT, false>(a, d, acc, slot, stage); break;
+    case MODE_SELECT: phase_select<DT>(a, d, acc, stage); break;
     default: break;
     }
 }
@@ -468,6 +553,7 @@ __device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, Blo
 template <int DT>
 __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
+    __shared__ WarpStage stage[kMaxWarps];
     __shared__ Desc s_desc;
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
@@ -481,7 +567,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
         __syncthreads();
         const Desc d = s_desc;
         if (d.mode == MODE_DONE) break;
-        run_phase<DT>(a, d, acc, slot);
+        run_phase<DT>(a, d, acc, slot, stage);
         if (!grid_barrier<DT>(a, acc, &s_ok)) break;
     }
     __syncthreads();
@@ -492,6 +578,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
 template <int DT, uint32_t MODE>
 __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
+    __shared__ WarpStage stage[kMaxWarps];
     __shared__ Desc s_desc;
     __shared__ BlockAcc acc;
     if (threadIdx.x == 0) {
@@ -502,7 +589,7 @@ __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __syncthreads();
     const Desc d = s_desc;
     if (d.mode != MODE) return;
-    run_phase<DT>(a, d, acc, slot);
+    run_phase<DT>(a, d, acc, slot, stage);
     __syncthreads();
     if (threadIdx.x == 0) {
         flush_far_min(a.ctl, acc, inf_key<DT>());
