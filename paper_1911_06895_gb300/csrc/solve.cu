@@ -35,6 +35,7 @@ namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
+constexpr int kIlp = 4;                // independent 32-arc steps per warp iteration
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -190,22 +191,15 @@ __device__ __forceinline__ void queue_near(const SolveArgs &a, const Desc &d, ui
     if (mark_far && __ldcg(a.far_flag + v) == 1u) a.far_flag[v] = 2u;
 }
 
-// relax(v, new_dist) of Section III-C on the packed word.
+// relax(v, new_dist) of Section III-C, after the packed atomicMin found a strict
+// decrease of t[v]: v re-enters bucket i ((t_Req < t) o t_Bi) or goes to the far pile.
 template <int DT>
-__device__ __forceinline__ void relax_arc(const SolveArgs &a, const Desc &d, uint32_t v, uint32_t ckey,
-                                          uint32_t u, Push &p, uint32_t &far_min, uint32_t &improved) {
-    if (ckey >= inf_key<DT>()) return;
-    const unsigned long long cand = ((unsigned long long)ckey << 32) | u;
-    // packed[v] only decreases, so any earlier value is an upper bound: skip the
-    // atomic when the request cannot win
-    if (cand >= __ldcg(a.packed + v)) return;
-    const unsigned long long old = atomicMin(a.packed + v, cand);
-    if (cand >= old) return;
-    if ((uint32_t)(old >> 32) <= ckey) return;         // equal distance: predecessor tie-break only
+__device__ __forceinline__ void on_improved(const SolveArgs &a, const Desc &d, uint32_t v, uint32_t ckey,
+                                            Push &p, uint32_t &far_min, uint32_t &improved) {
     ++improved;
-    if (ckey < d.T) {                                  // (t_Req < t) o t_Bi: back into bucket i
+    if (ckey < d.T) {
         queue_near(a, d, v, p, true);
-    } else {                                           // a later bucket: far pile
+    } else {
         far_min = min(far_min, ckey);
         p.far = atomicExch(a.far_flag + v, 1u) == 0u;
     }
@@ -299,42 +293,76 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
         };
         load_window(jw);
         int *sl = slot + (threadIdx.x >> 5) * 32;
-        for (uint32_t base = e0; base < e1; base += 32u) {
-            const uint32_t last = min(base + 31u, e1 - 1u);
-            if (last >= wend) {
-                // move the window to the owner of `base` (inside it, or the entry just past it)
-                const uint32_t shift = base >= wend ? 32u : 31u - __clz(__ballot_sync(FULL, woff <= base));
-                jw += shift;
-                load_window(jw);
-            }
-            // owner of arc base + lane: the last window entry starting at or before it
-            const int carry = 31 - __clz(__ballot_sync(FULL, woff <= base));
-            sl[lane] = -1;
-            __syncwarp();
-            if (woff > base && woff - base < 32u) sl[woff - base] = (int)lane;
-            __syncwarp();
-            int own = sl[lane];
+        // Each iteration maps kIlp 32-arc steps to owners first, then issues their
+        // arc loads, distance reads and atomics back to back, so a warp keeps
+        // kIlp independent relaxations per lane in flight.
+        for (uint32_t base0 = e0; base0 < e1; base0 += 32u * kIlp) {
+            uint32_t ai[kIlp], ov[kIlp], okey[kIlp];
+            bool ok[kIlp];
             #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int t = __shfl_up_sync(FULL, own, o);
-                if ((int)lane >= o) own = max(own, t);
+            for (int k = 0; k < kIlp; ++k) {
+                const uint32_t base = base0 + 32u * (uint32_t)k;
+                ok[k] = false;
+                ai[k] = 0u;
+                ov[k] = 0u;
+                okey[k] = inf_key<DT>();
+                if (base < e1) {
+                    const uint32_t last = min(base + 31u, e1 - 1u);
+                    if (last >= wend) {
+                        // move the window to the owner of `base` (inside it, or the entry just past it)
+                        const uint32_t shift = base >= wend ? 32u : 31u - __clz(__ballot_sync(FULL, woff <= base));
+                        jw += shift;
+                        load_window(jw);
+                    }
+                    // owner of arc base + lane: the last window entry starting at or before it
+                    const int carry = 31 - __clz(__ballot_sync(FULL, woff <= base));
+                    sl[lane] = -1;
+                    __syncwarp();
+                    if (woff > base && woff - base < 32u) sl[woff - base] = (int)lane;
+                    __syncwarp();
+                    int own = sl[lane];
+                    #pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int t = __shfl_up_sync(FULL, own, o);
+                        if ((int)lane >= o) own = max(own, t);
+                    }
+                    own = max(own, carry);
+                    __syncwarp();
+                    ov[k] = __shfl_sync(FULL, wv, own);
+                    const uint32_t ooff = __shfl_sync(FULL, woff, own);
+                    const uint32_t obeg = __shfl_sync(FULL, wbeg, own);
+                    okey[k] = __shfl_sync(FULL, wkey, own);
+                    const uint32_t e = base + lane;
+                    ai[k] = obeg + (e - ooff);
+                    ok[k] = e < e1 && ai[k] < a.m;     // defensive bound; true when lists are consistent
+                }
             }
-            own = max(own, carry);
-            __syncwarp();
-            const uint32_t ov = __shfl_sync(FULL, wv, own);
-            const uint32_t ooff = __shfl_sync(FULL, woff, own);
-            const uint32_t obeg = __shfl_sync(FULL, wbeg, own);
-            const uint32_t okey = __shfl_sync(FULL, wkey, own);
-            const uint32_t e = base + lane;
-            Push p{};
-            uint32_t v = 0;
-            const uint32_t ai = obeg + (e - ooff);
-            if (e < e1 && ai < a.m) {                 // defensive bound; always true when lists are consistent
-                const uint2 arc = a.arcs[ai];
-                v = arc.x;
-                relax_arc<DT>(a, d, v, key_add<DT>(okey, arc.y), ov, p, far_min, improved);
+            uint2 arc[kIlp];
+            #pragma unroll
+            for (int k = 0; k < kIlp; ++k) arc[k] = ok[k] ? a.arcs[ai[k]] : make_uint2(0u, 0u);
+            uint32_t ck[kIlp];
+            unsigned long long cur[kIlp];
+            #pragma unroll
+            for (int k = 0; k < kIlp; ++k) {
+                ck[k] = ok[k] ? key_add<DT>(okey[k], arc[k].y) : inf_key<DT>();
+                cur[k] = ck[k] < inf_key<DT>() ? __ldcg(a.packed + arc[k].x) : 0ull;
             }
-            stage_pushes(q, ws, p, v);
+            // packed[v] only decreases, so a value read earlier bounds it from above:
+            // the atomic is skipped when the request cannot win (old = 0 means no win)
+            unsigned long long old[kIlp];
+            #pragma unroll
+            for (int k = 0; k < kIlp; ++k) {
+                const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
+                old[k] = (ck[k] < inf_key<DT>() && cand < cur[k]) ? atomicMin(a.packed + arc[k].x, cand) : 0ull;
+            }
+            #pragma unroll
+            for (int k = 0; k < kIlp; ++k) {
+                Push p{};
+                const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
+                if (cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k])      // strict distance decrease
+                    on_improved<DT>(a, d, arc[k].x, ck[k], p, far_min, improved);
+                stage_pushes(q, ws, p, arc[k].x);
+            }
         }
         drain_pushes(q, ws);
         if (lane == 0) {
