@@ -179,7 +179,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sources", type=int, default=0, help="CPU baseline sample (0: one per core)")
+    ap.add_argument("--profile-solves", type=int, default=0,
+                    help="profiling driver: run this many solves at --profile-delta and exit (for ncu)")
+    ap.add_argument("--profile-delta", type=float, default=0.1)
     args = ap.parse_args()
+    if args.profile_solves:
+        profile_driver(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -324,6 +330,20 @@ def main():
     if dist_pg:
         dist_pg.barrier()
         dist_pg.destroy_process_group()
+
+
+def profile_driver(args):
+    """A fixed, short sequence of solves for profilers: split, then N solves."""
+    import torch
+    import paper_1911_06895_gb300 as ds
+    g, srcs, _ = build_workload(args.scale, max(args.profile_solves, 1), 0)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    h.prepare(args.profile_delta)
+    opt = ds.make_options(mode=args.mode)
+    for s in srcs[:args.profile_solves]:
+        r = h.solve(s, args.profile_delta, options=opt, stats=True)
+        print(json.dumps({"src": s, "delta": args.profile_delta, **r.stats}), flush=True)
+    torch.cuda.synchronize()
 
 
 def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args):
