@@ -12,16 +12,16 @@
 //           then the far pile is compacted into F and S (Fig. 1's outer loop;
 //           empty buckets are skipped).
 // A vertex whose distance strictly decreases into bucket <= i is queued once
-// per round: its light segment goes to the next F and, once per bucket, its
+// per phase: its light segment goes to the next F and, once per bucket, its
 // heavy segment to S (S = S u t_Bi, Fig. 1). A decrease into a later bucket
-// puts it on the far pile.
+// puts it on the far pile (two levels, see dsssp_internal.cuh).
 //
 // Load balance: F and S entries carry their arc offset within the list, so a
 // phase splits the list's flattened arcs into equal contiguous slices, one per
 // warp (merge-path). Each warp finds its first entry with a 32-ary search and
-// walks a 32-entry window of the list; every 32-arc step maps arcs to owners
-// with one scatter and a prefix-max. A hub's arcs are thus spread over the
-// whole grid and a phase costs (its arcs) / (all warps).
+// walks a 32-entry window of the list; each 32-arc step maps arcs to owners
+// (one entry for all lanes, or a scatter and a prefix-max). A hub's arcs are
+// spread over the whole grid. A warp keeps kIlp steps in flight.
 //
 // DSSSP_MODE_PERSISTENT runs all phases in one cooperative launch; every
 // barrier wait is bounded by timeout_ns and ends the kernel with
@@ -36,6 +36,9 @@ namespace {
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 constexpr int kIlp = 4;                // independent 32-arc steps per warp iteration
+constexpr uint32_t kMinSlice = 32u * kIlp;
+
+enum FarFlag : uint32_t { FAR_NONE = 0, FAR_FN = 1, FAR_FN_STALE = 2, FAR_FF = 3, FAR_FF_STALE = 4 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -54,13 +57,31 @@ __device__ __forceinline__ uint64_t globaltimer() {
 template <typename T>
 __device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; }
 
-// Per-warp staging of pushes in shared memory. A list counter is touched once
-// per 32 staged entries instead of once per 32-arc step, which removes the
-// serialization of many warps' atomics on the same three counters.
+// d (+) w on keys: float32 add rounded to nearest (+inf on overflow), or int32
+// add saturated at INT32_MAX. Both operands are below 2^31 for int32.
+template <int DT>
+__device__ __forceinline__ uint32_t key_add(uint32_t dkey, uint32_t wbits) {
+    if (DT == DSSSP_F32) {
+        return __float_as_uint(__fadd_rn(__uint_as_float(dkey), __uint_as_float(wbits)));
+    } else {
+        uint32_t s = dkey + wbits;
+        return s >= KEY_INF_I32 ? KEY_INF_I32 : s;
+    }
+}
+
+template <int DT>
+__device__ __forceinline__ constexpr uint32_t inf_key() {
+    return DT == DSSSP_F32 ? KEY_INF_F32 : KEY_INF_I32;
+}
+
+// ---------------------------------------------------------------------------
+// Per-warp staging of pushes in shared memory: a list counter is touched once
+// per 32 staged entries, not once per 32-arc step, and list stores are 32-wide.
 struct WarpStage {
     uint32_t fv[64], fd[64], fb[64];     // next-frontier entries (vertex, light degree, begin)
     uint32_t sv[64], sd[64], sb[64];     // S entries (vertex, heavy degree, begin)
-    uint32_t far[64];                    // far-pile entries
+    uint32_t fn[64];                     // far pile, near level
+    uint32_t ff[64];                     // far pile, outer level
 };
 
 // Write n <= 32 staged segment entries (lanes < n) to an F or S list.
@@ -135,75 +156,28 @@ __device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, ui
     }
 }
 
-// d (+) w on keys: float32 add rounded to nearest (+inf on overflow), or int32
-// add saturated at INT32_MAX. Both operands are below 2^31 for int32.
-template <int DT>
-__device__ __forceinline__ uint32_t key_add(uint32_t dkey, uint32_t wbits) {
-    if (DT == DSSSP_F32) {
-        return __float_as_uint(__fadd_rn(__uint_as_float(dkey), __uint_as_float(wbits)));
-    } else {
-        uint32_t s = dkey + wbits;
-        return s >= KEY_INF_I32 ? KEY_INF_I32 : s;
-    }
-}
-
-template <int DT>
-__device__ __forceinline__ constexpr uint32_t inf_key() {
-    return DT == DSSSP_F32 ? KEY_INF_F32 : KEY_INF_I32;
-}
-
+// ---------------------------------------------------------------------------
 // Per-phase constants every block reads from the control block after a barrier.
 struct Desc {
-    uint32_t mode, cur, scur, far_cur, qstamp, sround, T;
+    uint32_t mode, cur, scur, fn_cur, ff_cur, rescan_ff, qstamp, sround, T, Tw;
     uint32_t spush;       // S list receiving pushes in this phase
     uint32_t sstamp;      // S stamp of those pushes
-    uint32_t count;       // entries of the list this phase reads
-    uint32_t arcs;        // arcs of that list (LIGHT / HEAVY)
+    uint32_t count;       // entries of the list this phase reads (SELECT: FN part)
+    uint32_t count2;      // SELECT: FF entries re-examined
+    uint32_t arcs;        // arcs of the list (LIGHT / HEAVY)
 };
 
 // Block-local accumulators flushed to the control block.
 struct BlockAcc {
-    uint32_t far_min;
+    uint32_t fn_min, ff_min;
     unsigned long long arcs_light, arcs_heavy, improvements, far_scanned;
 };
 
 // Pending pushes of one lane in one step.
 struct Push {
-    bool f, s, far;
+    bool f, s, fn, ff;
     uint32_t fdeg, fbeg, sdeg, sbeg;
 };
-
-// Queue v for bucket i (its key is now below T): once per round into the next
-// F (its light segment), once per bucket into S (its heavy segment). A live
-// far-pile entry of v becomes stale.
-__device__ __forceinline__ void queue_near(const SolveArgs &a, const Desc &d, uint32_t v, Push &p, bool mark_far) {
-    if (atomicExch(a.near_stamp + v, d.qstamp) == d.qstamp) return;
-    const uint4 vi = a.vinfo[v];
-    p.fdeg = vi.y - vi.x;
-    p.fbeg = vi.x;
-    p.f = p.fdeg != 0u;
-    if (__ldcg(a.s_stamp + v) != d.sstamp) {
-        a.s_stamp[v] = d.sstamp;
-        p.sdeg = vi.z - vi.y;
-        p.sbeg = vi.y;
-        p.s = p.sdeg != 0u;
-    }
-    if (mark_far && __ldcg(a.far_flag + v) == 1u) a.far_flag[v] = 2u;
-}
-
-// relax(v, new_dist) of Section III-C, after the packed atomicMin found a strict
-// decrease of t[v]: v re-enters bucket i ((t_Req < t) o t_Bi) or goes to the far pile.
-template <int DT>
-__device__ __forceinline__ void on_improved(const SolveArgs &a, const Desc &d, uint32_t v, uint32_t ckey,
-                                            Push &p, uint32_t &far_min, uint32_t &improved) {
-    ++improved;
-    if (ckey < d.T) {
-        queue_near(a, d, v, p, true);
-    } else {
-        far_min = min(far_min, ckey);
-        p.far = atomicExch(a.far_flag + v, 1u) == 0u;
-    }
-}
 
 // The lists a phase pushes into, and the warp's staged counts.
 struct PushCtx {
@@ -211,56 +185,111 @@ struct PushCtx {
     unsigned long long *ctrF;
     uint4 *S;
     unsigned long long *ctrS;
-    uint32_t *FAR;
-    uint32_t *nFar;
-    uint32_t nf, ns, nfar;
+    uint32_t *FN, *nFN, *FF, *nFF;
+    uint32_t nf, ns, nfn, nff;
 };
 
-__device__ __forceinline__ PushCtx push_ctx(const SolveArgs &a, const Desc &d) {
+// far pushes of LIGHT/HEAVY extend the current far lists; SELECT writes the next ones
+__device__ __forceinline__ PushCtx push_ctx(const SolveArgs &a, const Desc &d, bool select) {
     Ctl *c = a.ctl;
     PushCtx q;
     q.F = d.cur ? a.F0 : a.F1;
     q.ctrF = &c->ctrF[d.cur ^ 1u];
     q.S = d.spush ? a.S1 : a.S0;
     q.ctrS = &c->ctrS[d.spush];
-    q.FAR = d.far_cur ? a.FAR1 : a.FAR0;
-    q.nFar = &c->nFar[d.far_cur];
-    q.nf = q.ns = q.nfar = 0u;
+    const uint32_t fn = select ? d.fn_cur ^ 1u : d.fn_cur;
+    const uint32_t ff = (select && d.rescan_ff) ? d.ff_cur ^ 1u : d.ff_cur;
+    q.FN = fn ? a.FN1 : a.FN0;
+    q.nFN = &c->nFN[fn];
+    q.FF = ff ? a.FF1 : a.FF0;
+    q.nFF = &c->nFF[ff];
+    q.nf = q.ns = q.nfn = q.nff = 0u;
     return q;
 }
 
 __device__ __forceinline__ void stage_pushes(PushCtx &q, WarpStage &ws, const Push &p, uint32_t v) {
+    if (__ballot_sync(FULL, p.f || p.s || p.fn || p.ff) == 0u) return;
     stage_seg(p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
     stage_seg(p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-    stage_id(p.far, v, ws.far, q.nfar, q.FAR, q.nFar);
+    stage_id(p.fn, v, ws.fn, q.nfn, q.FN, q.nFN);
+    stage_id(p.ff, v, ws.ff, q.nff, q.FF, q.nFF);
 }
 
 // Flush the partially filled staging buffers (end of a phase).
 __device__ __forceinline__ void drain_pushes(PushCtx &q, WarpStage &ws) {
     if (q.nf) flush_seg(ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
     if (q.ns) flush_seg(ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-    if (q.nfar) flush_ids(ws.far, q.nfar, q.FAR, q.nFar);
+    if (q.nfn) flush_ids(ws.fn, q.nfn, q.FN, q.nFN);
+    if (q.nff) flush_ids(ws.ff, q.nff, q.FF, q.nFF);
     __syncwarp();
-    q.nf = q.ns = q.nfar = 0u;
+    q.nf = q.ns = q.nfn = q.nff = 0u;
 }
 
-// LIGHT / HEAVY: relax the arcs of a list, split evenly over all warps.
+// Queue v for bucket i (its key is now below T): once per phase into the next
+// F (its light segment), once per bucket into S (its heavy segment). A live
+// far-pile entry of v becomes stale. The loads are issued together with the
+// stamp exchange; they are simply unused when v is already queued.
+__device__ __forceinline__ void queue_near(const SolveArgs &a, const Desc &d, uint32_t v, Push &p, bool mark_far) {
+    const uint32_t prev = atomicExch(a.near_stamp + v, d.qstamp);
+    const uint4 vi = a.vinfo[v];
+    const uint32_t ss = __ldcg(a.s_stamp + v);
+    const uint32_t ff = mark_far ? __ldcg(a.far_flag + v) : FAR_NONE;
+    if (prev == d.qstamp) return;
+    p.fdeg = vi.y - vi.x;
+    p.fbeg = vi.x;
+    p.f = p.fdeg != 0u;
+    if (ss != d.sstamp) {
+        a.s_stamp[v] = d.sstamp;
+        p.sdeg = vi.z - vi.y;
+        p.sbeg = vi.y;
+        p.s = p.sdeg != 0u;
+    }
+    if (ff == FAR_FN || ff == FAR_FF) a.far_flag[v] = ff + 1u;
+}
+
+// relax(v, new_dist) of Section III-C, after the packed atomicMin found a strict
+// decrease of t[v]: v re-enters bucket i ((t_Req < t) o t_Bi) or goes to the far pile.
+template <int DT>
+__device__ __forceinline__ void on_improved(const SolveArgs &a, const Desc &d, uint32_t v, uint32_t ckey,
+                                            Push &p, uint32_t &fn_min, uint32_t &ff_min, uint32_t &improved) {
+    ++improved;
+    if (ckey < d.T) {
+        queue_near(a, d, v, p, true);
+        return;
+    }
+    const uint32_t want = ckey < d.Tw ? FAR_FN : FAR_FF;
+    uint32_t old = atomicCAS(a.far_flag + v, FAR_NONE, want);
+    if (old == FAR_NONE) {
+        old = want;
+        if (want == FAR_FN) p.fn = true; else p.ff = true;
+    } else if (old == FAR_FN_STALE || old == FAR_FF_STALE) {
+        // cannot happen for a settled vertex; revive the existing entry to stay safe
+        atomicCAS(a.far_flag + v, old, old - 1u);
+        old -= 1u;
+    }
+    if (old == FAR_FN) fn_min = min(fn_min, ckey); else ff_min = min(ff_min, ckey);
+}
+
+// LIGHT / HEAVY: relax the arcs of a list, split evenly over the warps.
 template <int DT, bool LIGHT>
 __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot, WarpStage *stage) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t nw_all = (gridDim.x * blockDim.x) >> 5;
     const uint4 *list = LIGHT ? (d.cur ? a.F1 : a.F0) : (d.scur ? a.S1 : a.S0);
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[4 * j]
     const uint32_t count = d.count;
     const uint32_t E = d.arcs;
-    const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
-    const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
-    uint32_t far_min = inf_key<DT>();
+    // at least kMinSlice arcs per warp: small phases use few warps
+    const uint32_t want_w = (E + kMinSlice - 1u) / kMinSlice;
+    const uint32_t nw = want_w < nw_all ? want_w : nw_all;
+    uint32_t fn_min = inf_key<DT>(), ff_min = inf_key<DT>();
     uint32_t improved = 0;
-    PushCtx q = push_ctx(a, d);
-    WarpStage &ws = stage[threadIdx.x >> 5];
-    if (e0 < e1) {
+    if (gw < nw) {
+        const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
+        const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
+        PushCtx q = push_ctx(a, d, false);
+        WarpStage &ws = stage[threadIdx.x >> 5];
         // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
         uint32_t lo = 0, hi = count;
         while (hi - lo > 32u) {
@@ -281,7 +310,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
         auto load_window = [&](uint32_t j) {
             const uint32_t idx = j + lane;
             if (idx < count) {
-                const uint4 en = __ldcg(list + idx);
+                const uint4 en = __ldcs(list + idx);
                 wv = en.x < a.n ? en.x : 0u;          // defensive: ids come from device lists
                 woff = en.y;
                 wbeg = en.z;
@@ -294,8 +323,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
         load_window(jw);
         int *sl = slot + (threadIdx.x >> 5) * 32;
         // Each iteration maps kIlp 32-arc steps to owners first, then issues their
-        // arc loads, distance reads and atomics back to back, so a warp keeps
-        // kIlp independent relaxations per lane in flight.
+        // arc loads, distance reads and atomics back to back.
         for (uint32_t base0 = e0; base0 < e1; base0 += 32u * kIlp) {
             uint32_t ai[kIlp], ov[kIlp], okey[kIlp];
             bool ok[kIlp];
@@ -316,18 +344,23 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
                     }
                     // owner of arc base + lane: the last window entry starting at or before it
                     const int carry = 31 - __clz(__ballot_sync(FULL, woff <= base));
-                    sl[lane] = -1;
-                    __syncwarp();
-                    if (woff > base && woff - base < 32u) sl[woff - base] = (int)lane;
-                    __syncwarp();
-                    int own = sl[lane];
-                    #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const int t = __shfl_up_sync(FULL, own, o);
-                        if ((int)lane >= o) own = max(own, t);
+                    const uint32_t next_off = __shfl_sync(FULL, woff, (carry + 1) & 31);
+                    const bool one_owner = carry == 31 ? wend > base + 31u : next_off > base + 31u;
+                    int own = carry;
+                    if (!one_owner) {
+                        sl[lane] = -1;
+                        __syncwarp();
+                        if (woff > base && woff - base < 32u) sl[woff - base] = (int)lane;
+                        __syncwarp();
+                        own = sl[lane];
+                        #pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int t = __shfl_up_sync(FULL, own, o);
+                            if ((int)lane >= o) own = max(own, t);
+                        }
+                        own = max(own, carry);
+                        __syncwarp();
                     }
-                    own = max(own, carry);
-                    __syncwarp();
                     ov[k] = __shfl_sync(FULL, wv, own);
                     const uint32_t ooff = __shfl_sync(FULL, woff, own);
                     const uint32_t obeg = __shfl_sync(FULL, wbeg, own);
@@ -339,7 +372,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
             }
             uint2 arc[kIlp];
             #pragma unroll
-            for (int k = 0; k < kIlp; ++k) arc[k] = ok[k] ? a.arcs[ai[k]] : make_uint2(0u, 0u);
+            for (int k = 0; k < kIlp; ++k) arc[k] = ok[k] ? __ldcs(a.arcs + ai[k]) : make_uint2(0u, 0u);
             uint32_t ck[kIlp];
             unsigned long long cur[kIlp];
             #pragma unroll
@@ -360,7 +393,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
                 Push p{};
                 const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
                 if (cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k])      // strict distance decrease
-                    on_improved<DT>(a, d, arc[k].x, ck[k], p, far_min, improved);
+                    on_improved<DT>(a, d, arc[k].x, ck[k], p, fn_min, ff_min, improved);
                 stage_pushes(q, ws, p, arc[k].x);
             }
         }
@@ -370,54 +403,57 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
         }
     }
-    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
+    if (fn_min < inf_key<DT>()) atomicMin(&acc.fn_min, fn_min);
+    if (ff_min < inf_key<DT>()) atomicMin(&acc.ff_min, ff_min);
     if (improved) atomicAdd(&acc.improvements, (unsigned long long)improved);
 }
 
 // SELECT: compact the far pile. Live entries whose key is below T (bucket <= i)
-// are queued into F and S; the rest stay, and their minimum key bounds the
-// next bucket; stale entries are dropped.
+// are queued into F and S; the rest stay (FF entries below the new window move
+// to FN), and their minimum keys bound the next bucket; stale entries are dropped.
 template <int DT>
 __device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc, WarpStage *stage) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    Ctl *c = a.ctl;
-    const uint32_t *in = d.far_cur ? a.FAR1 : a.FAR0;
-    uint32_t *out = d.far_cur ? a.FAR0 : a.FAR1;
-    uint32_t *out_cnt = &c->nFar[d.far_cur ^ 1u];
-    uint32_t far_min = inf_key<DT>();
-    const uint32_t count = d.count;
-    PushCtx q = push_ctx(a, d);
+    const uint32_t *fn_in = d.fn_cur ? a.FN1 : a.FN0;
+    const uint32_t *ff_in = d.ff_cur ? a.FF1 : a.FF0;
+    const uint32_t nfn = d.count, total = d.count + d.count2;
+    uint32_t fn_min = inf_key<DT>(), ff_min = inf_key<DT>();
+    PushCtx q = push_ctx(a, d, true);
     WarpStage &ws = stage[threadIdx.x >> 5];
-    uint32_t nkeep = 0;
-    for (unsigned long long base = (unsigned long long)gw * 32u; base < count; base += (unsigned long long)nw * 32u) {
+    for (unsigned long long base = (unsigned long long)gw * 32u; base < total; base += (unsigned long long)nw * 32u) {
         const uint32_t idx = (uint32_t)base + lane;
         Push p{};
-        bool keep = false;
         uint32_t v = 0;
-        if (idx < count && (v = __ldcg(in + idx)) < a.n) {
-            if (__ldcg(a.far_flag + v) == 1u) {
+        if (idx < total) {
+            const bool from_fn = idx < nfn;
+            v = from_fn ? __ldcs(fn_in + idx) : __ldcs(ff_in + (idx - nfn));
+            const uint32_t live = from_fn ? FAR_FN : FAR_FF;
+            const uint32_t f = v < a.n ? __ldcg(a.far_flag + v) : FAR_NONE;
+            if (v < a.n && f == live) {
                 const uint32_t k = (uint32_t)(__ldcg(a.packed + v) >> 32);
                 if (k < d.T) {
-                    a.far_flag[v] = 0u;
+                    a.far_flag[v] = FAR_NONE;
                     queue_near(a, d, v, p, false);
+                } else if (from_fn || k < d.Tw) {
+                    if (!from_fn) a.far_flag[v] = FAR_FN;
+                    p.fn = true;
+                    fn_min = min(fn_min, k);
                 } else {
-                    keep = true;
-                    far_min = min(far_min, k);
+                    p.ff = true;
+                    ff_min = min(ff_min, k);
                 }
-            } else {
-                a.far_flag[v] = 0u;
+            } else if (v < a.n && f == live + 1u) {
+                a.far_flag[v] = FAR_NONE;          // stale entry dropped
             }
         }
-        stage_seg(p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
-        stage_seg(p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-        stage_id(keep, v, ws.far, nkeep, out, out_cnt);
+        stage_pushes(q, ws, p, v);
     }
     drain_pushes(q, ws);
-    if (nkeep) flush_ids(ws.far, nkeep, out, out_cnt);
-    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&acc.far_scanned, (unsigned long long)count);
+    if (fn_min < inf_key<DT>()) atomicMin(&acc.fn_min, fn_min);
+    if (ff_min < inf_key<DT>()) atomicMin(&acc.ff_min, ff_min);
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&acc.far_scanned, (unsigned long long)total);
 }
 
 // ---------------------------------------------------------------------------
@@ -454,8 +490,13 @@ __device__ void serial_step(const SolveArgs &a) {
         break;
     case MODE_SELECT:
         c->st[ST_SELECT] += 1;
-        c->nFar[c->far_cur] = 0u;
-        c->far_cur ^= 1u;
+        c->nFN[c->fn_cur] = 0u;
+        c->fn_cur ^= 1u;
+        if (c->rescan_ff) {
+            c->st[ST_FFSCANS] += 1;
+            c->nFF[c->ff_cur] = 0u;
+            c->ff_cur ^= 1u;
+        }
         break;
     default:
         return;
@@ -474,21 +515,30 @@ __device__ void serial_step(const SolveArgs &a) {
         return;
     }
     // next non-empty bucket
-    const uint32_t fm = c->far_min;
+    const uint32_t fm = min(c->fn_min, c->ff_min);
     if (fm >= inf_key<DT>()) {
-        if (c->nFar[c->far_cur] == 0u) {
+        if (c->nFN[c->fn_cur] == 0u && c->nFF[c->ff_cur] == 0u) {
             c->mode = MODE_DONE;
             c->st[ST_NSTOTAL] = (long long)(now - c->t_start);
             return;
         }
         c->T = 0u;                              // only stale entries remain: drop them
+        c->Tw = 0u;
+        c->rescan_ff = c->nFF[c->ff_cur] != 0u;
     } else {
         const int64_t i = bucket_of_key(fm, DT, a.delta);
         c->bucket = i;
         c->T = i < INT64_MAX ? bucket_floor_key(i + 1, DT, a.delta) : 0u;
         if (c->T <= fm) c->T = fm + 1u;         // always take the smallest live key
+        c->rescan_ff = c->ff_min < c->T;
+        if (c->rescan_ff) {
+            const int64_t w = (int64_t)a.far_window;
+            c->Tw = i < INT64_MAX - w ? bucket_floor_key(i + w, DT, a.delta) : inf_key<DT>();
+            if (c->Tw < c->T) c->Tw = c->T;
+        }
     }
-    c->far_min = inf_key<DT>();
+    c->fn_min = inf_key<DT>();
+    if (c->rescan_ff) c->ff_min = inf_key<DT>();
     c->mode = MODE_SELECT;
 }
 
@@ -496,20 +546,27 @@ __device__ __forceinline__ void read_desc(const Ctl *c, Desc &d) {
     d.mode = vload(&c->mode);
     d.cur = vload(&c->cur);
     d.scur = vload(&c->scur);
-    d.far_cur = vload(&c->far_cur);
+    d.fn_cur = vload(&c->fn_cur);
+    d.ff_cur = vload(&c->ff_cur);
+    d.rescan_ff = vload(&c->rescan_ff);
     d.qstamp = vload(&c->qstamp);
     d.sround = vload(&c->sround);
     d.T = vload(&c->T);
+    d.Tw = vload(&c->Tw);
     // S pushes: into the current S, except during a heavy pass, which feeds the next one
     d.spush = d.mode == MODE_HEAVY ? d.scur ^ 1u : d.scur;
     d.sstamp = d.mode == MODE_HEAVY ? d.sround + 1u : d.sround;
     d.count = 0;
+    d.count2 = 0;
     d.arcs = 0;
     unsigned long long ctr = 0;
     switch (d.mode) {
     case MODE_LIGHT: ctr = vload(&c->ctrF[d.cur]); break;
     case MODE_HEAVY: ctr = vload(&c->ctrS[d.scur]); break;
-    case MODE_SELECT: d.count = vload(&c->nFar[d.far_cur]); break;
+    case MODE_SELECT:
+        d.count = vload(&c->nFN[d.fn_cur]);
+        d.count2 = d.rescan_ff ? vload(&c->nFF[d.ff_cur]) : 0u;
+        break;
     default: break;
     }
     if (d.mode == MODE_LIGHT || d.mode == MODE_HEAVY) {
@@ -519,10 +576,8 @@ __device__ __forceinline__ void read_desc(const Ctl *c, Desc &d) {
 }
 
 __device__ __forceinline__ void flush_far_min(Ctl *c, BlockAcc &acc, uint32_t inf) {
-    if (acc.far_min < inf) {
-        atomicMin(&c->far_min, acc.far_min);
-        acc.far_min = inf;
-    }
+    if (acc.fn_min < inf) { atomicMin(&c->fn_min, acc.fn_min); acc.fn_min = inf; }
+    if (acc.ff_min < inf) { atomicMin(&c->ff_min, acc.ff_min); acc.ff_min = inf; }
 }
 
 __device__ __forceinline__ void flush_stats(Ctl *c, BlockAcc &acc) {
@@ -530,6 +585,12 @@ __device__ __forceinline__ void flush_stats(Ctl *c, BlockAcc &acc) {
     if (acc.arcs_heavy) atomicAdd((unsigned long long *)&c->st[ST_AHEAVY], acc.arcs_heavy);
     if (acc.improvements) atomicAdd((unsigned long long *)&c->st[ST_IMPROVE], acc.improvements);
     if (acc.far_scanned) atomicAdd((unsigned long long *)&c->st[ST_FARSCAN], acc.far_scanned);
+    acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
+}
+
+template <int DT>
+__device__ __forceinline__ void acc_init(BlockAcc &acc) {
+    acc.fn_min = acc.ff_min = inf_key<DT>();
     acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
 }
 
@@ -586,10 +647,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
     if (a.test_hook == DSSSP_HOOK_STALL_BARRIER && blockIdx.x == 1) return;
-    if (threadIdx.x == 0) {
-        acc.far_min = inf_key<DT>();
-        acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
-    }
+    if (threadIdx.x == 0) acc_init<DT>(acc);
     for (;;) {
         if (threadIdx.x == 0) read_desc(a.ctl, s_desc);
         __syncthreads();
@@ -611,8 +669,7 @@ __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __shared__ BlockAcc acc;
     if (threadIdx.x == 0) {
         read_desc(a.ctl, s_desc);
-        acc.far_min = inf_key<DT>();
-        acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
+        acc_init<DT>(acc);
     }
     __syncthreads();
     const Desc d = s_desc;
@@ -639,7 +696,7 @@ __global__ void k_init(SolveArgs a) {
         // t = inf, t[s] = 0 (Fig. 1); the predecessor of s is s
         a.packed[v] = v == a.src ? (unsigned long long)a.src : unreached;
         a.near_stamp[v] = v == a.src ? 1u : 0u;
-        a.far_flag[v] = 0u;
+        a.far_flag[v] = FAR_NONE;
         a.s_stamp[v] = v == a.src ? 1u : 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -650,17 +707,22 @@ __global__ void k_init(SolveArgs a) {
         c->mode = MODE_LIGHT;     // B_0 = {s}
         c->cur = 0u;
         c->scur = 0u;
-        c->far_cur = 0u;
+        c->fn_cur = 0u;
+        c->ff_cur = 0u;
+        c->rescan_ff = 0u;
         c->qstamp = 1u;
         c->sround = 1u;
         c->bucket = 0;
         c->T = bucket_floor_key(1, DT, a.delta);
+        c->Tw = bucket_floor_key((int64_t)a.far_window, DT, a.delta);
+        if (c->Tw < c->T) c->Tw = c->T;
         c->ctrF[0] = (vs.y > vs.x) ? ((1ull << 32) | (vs.y - vs.x)) : 0ull;
         c->ctrF[1] = 0ull;
         c->ctrS[0] = (vs.z > vs.y) ? ((1ull << 32) | (vs.z - vs.y)) : 0ull;
         c->ctrS[1] = 0ull;
-        c->nFar[0] = c->nFar[1] = 0u;
-        c->far_min = inf_key<DT>();
+        c->nFN[0] = c->nFN[1] = 0u;
+        c->nFF[0] = c->nFF[1] = 0u;
+        c->fn_min = c->ff_min = inf_key<DT>();
         c->err = 0;
         c->phases = 0;
         for (int k = 0; k < 16; ++k) c->st[k] = 0;
