@@ -85,7 +85,7 @@ typedef struct {
     int32_t  mode;          /* dsssp_mode; default DSSSP_MODE_PERSISTENT                        */
     int32_t  block_size;    /* threads per block, multiple of 32, <= 512; default 512           */
     int32_t  grid_size;     /* blocks of the persistent kernel; default = all co-resident blocks */
-    int32_t  far_window;    /* buckets held in the near level of the far pile; default 8         */
+    int32_t  reserved0;     /* must be 0                                                         */
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
@@ -109,10 +109,9 @@ typedef struct {
     int64_t ns_heavy;         /* device time in heavy passes                                    */
     int64_t ns_select;        /* device time in next-bucket searches                           */
     int64_t ns_total;         /* device time of the whole solve kernel                          */
-    int64_t far_rescans;      /* next-bucket searches that re-examined the far pile's outer level */
     int64_t grid_size;        /* blocks used                                                    */
     int64_t block_size;       /* threads per block used                                          */
-    int64_t reserved[7];
+    int64_t reserved[8];
 } dsssp_stats;
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -142,10 +142,8 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     const size_t o_f1 = bytes;     bytes += up(n * 16);
     const size_t o_s0 = bytes;     bytes += up(n * 16);
     const size_t o_s1 = bytes;     bytes += up(n * 16);
-    const size_t o_fn0 = bytes;    bytes += up(n * 4);
-    const size_t o_fn1 = bytes;    bytes += up(n * 4);
-    const size_t o_ff0 = bytes;    bytes += up(n * 4);
-    const size_t o_ff1 = bytes;    bytes += up(n * 4);
+    const size_t o_far0 = bytes;   bytes += up(n * 4);
+    const size_t o_far1 = bytes;   bytes += up(n * 4);
     const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
     const size_t o_sticky = bytes; bytes += up(sizeof(int32_t));
     char *base = nullptr;
@@ -163,33 +161,31 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     a.F1 = (uint4 *)(base + o_f1);
     a.S0 = (uint4 *)(base + o_s0);
     a.S1 = (uint4 *)(base + o_s1);
-    a.FN0 = (uint32_t *)(base + o_fn0);
-    a.FN1 = (uint32_t *)(base + o_fn1);
-    a.FF0 = (uint32_t *)(base + o_ff0);
-    a.FF1 = (uint32_t *)(base + o_ff1);
+    a.FAR0 = (uint32_t *)(base + o_far0);
+    a.FAR1 = (uint32_t *)(base + o_far1);
     a.ctl = (Ctl *)(base + o_ctl);
     g->ctl = a.ctl;
     g->sticky = (int32_t *)(base + o_sticky);
     return DSSSP_OK;
 }
 
-void fill_stats(const Ctl &c, int grid, int block, dsssp_stats *s) {
+void fill_stats(const Ctl &ctl, int grid, int block, dsssp_stats *s) {
+    const long long *st = ctl.ss.st;
     std::memset(s, 0, sizeof *s);
-    s->buckets = c.st[ST_BUCKETS];
-    s->light_phases = c.st[ST_LIGHT];
-    s->heavy_phases = c.st[ST_HEAVY];
-    s->select_phases = c.st[ST_SELECT];
-    s->vertices_light = c.st[ST_VLIGHT];
-    s->vertices_heavy = c.st[ST_VHEAVY];
-    s->arcs_light = c.st[ST_ALIGHT];
-    s->arcs_heavy = c.st[ST_AHEAVY];
-    s->far_scanned = c.st[ST_FARSCAN];
-    s->improvements = c.st[ST_IMPROVE];
-    s->ns_light = c.st[ST_NSLIGHT];
-    s->ns_heavy = c.st[ST_NSHEAVY];
-    s->ns_select = c.st[ST_NSSELECT];
-    s->ns_total = c.st[ST_NSTOTAL];
-    s->far_rescans = c.st[ST_FFSCANS];
+    s->buckets = st[ST_BUCKETS];
+    s->light_phases = st[ST_LIGHT];
+    s->heavy_phases = st[ST_HEAVY];
+    s->select_phases = st[ST_SELECT];
+    s->vertices_light = st[ST_VLIGHT];
+    s->vertices_heavy = st[ST_VHEAVY];
+    s->arcs_light = st[ST_ALIGHT];
+    s->arcs_heavy = st[ST_AHEAVY];
+    s->far_scanned = st[ST_FARSCAN];
+    s->improvements = st[ST_IMPROVE];
+    s->ns_light = st[ST_NSLIGHT];
+    s->ns_heavy = st[ST_NSHEAVY];
+    s->ns_select = st[ST_NSSELECT];
+    s->ns_total = st[ST_NSTOTAL];
     s->grid_size = grid;
     s->block_size = block;
 }
@@ -223,7 +219,6 @@ dsssp_status dsssp_options_default(dsssp_options *opt) {
     opt->grid_size = 0;
     opt->max_phases = (int64_t)1 << 26;
     opt->timeout_ns = 2000000000LL;
-    opt->far_window = 8;
     return DSSSP_OK;
 }
 
@@ -323,13 +318,13 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
         opt.mode = opt_in->mode;
         if (opt_in->block_size) opt.block_size = opt_in->block_size;
         if (opt_in->grid_size) opt.grid_size = opt_in->grid_size;
-        if (opt_in->far_window) opt.far_window = opt_in->far_window;
+        if (opt_in->reserved0) return DSSSP_ERR_INVALID_ARG;
         if (opt_in->max_phases) opt.max_phases = opt_in->max_phases;
         if (opt_in->timeout_ns) opt.timeout_ns = opt_in->timeout_ns;
         opt.test_hook = opt_in->test_hook;
     }
     if (opt.block_size < 32 || opt.block_size > 512 || opt.block_size % 32 != 0) return DSSSP_ERR_INVALID_ARG;
-    if (opt.far_window < 1 || opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
+    if (opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
     if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED) return DSSSP_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -359,7 +354,6 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     a.max_phases = opt.max_phases;
     a.n = (uint32_t)g->n;
     a.m = (uint32_t)g->m;
-    a.far_window = (uint32_t)opt.far_window;
     a.src = (uint32_t)src;
     a.inf_key = key_inf(g->dtype);
     a.dtype = g->dtype;
@@ -374,7 +368,7 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
         for (int64_t ph = 0;; ++ph) {
             DSSSP_TRY(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
             DSSSP_TRY(cudaStreamSynchronize(st));
-            const uint32_t mode = g->ctl_host->mode;
+            const uint32_t mode = g->ctl_host->desc.mode;
             if (mode == MODE_DONE || g->ctl_host->err != 0) break;
             DSSSP_TRY(launch_phase_stepped(a, mode, grid, opt.block_size, st));
             DSSSP_TRY(launch_serial_step(a, st));

@@ -109,45 +109,56 @@ enum Mode : uint32_t {
 // on the list's counter, so entry positions and arc offsets are consistent and
 // a phase can split the list's flattened arcs evenly over all warps.
 //
-// The far pile (vertices whose tentative distance lies in a later bucket) has
-// two levels: FN holds keys below Tw (the next far_window buckets) and is
-// examined at every bucket change; FF holds the rest and is re-examined only
-// when its lower bound ff_min drops below the threshold of the next bucket.
-// far_flag[v]: 0 no entry, 1 live in FN, 2 stale in FN, 3 live in FF, 4 stale in FF.
-struct Ctl {
-    unsigned int bar_count;
-    unsigned int bar_gen;
-    // phase descriptor
+// Control block. The serial step of a barrier (one thread) loads SerialState
+// and the list counters in one batch, decides the next phase in registers and
+// publishes a PhaseDesc that every block reads with four 16-byte loads, so a
+// phase change costs a few memory round trips instead of one per field.
+
+// Everything a block needs to run a phase (64 bytes).
+struct alignas(64) PhaseDesc {
     uint32_t mode;
     uint32_t cur;           // F list being read (0/1); F pushes go to cur^1
-    uint32_t scur;          // S list holding the current bucket's S
-    uint32_t fn_cur;        // FN list being filled / read (0/1)
-    uint32_t ff_cur;        // FF list being filled / read (0/1)
-    uint32_t rescan_ff;     // this SELECT also re-examines FF
+    uint32_t scur;          // S list being read by a heavy pass
+    uint32_t spush;         // S list receiving pushes in this phase
+    uint32_t sstamp;        // S stamp of those pushes
+    uint32_t far_cur;       // far list being read (SELECT) or appended to
     uint32_t qstamp;        // stamp of pushes into the next frontier
-    uint32_t sround;        // stamp of membership in S[scur]
     uint32_t T;             // key < T  <=>  bucket <= i
-    uint32_t Tw;            // key < Tw: far entries go to FN, else FF
-    int64_t bucket;         // current bucket index i
-    // list counters: (entries << 32) | arcs
-    unsigned long long ctrF[2];
-    unsigned long long ctrS[2];
-    uint32_t nFN[2];
-    uint32_t nFF[2];
-    uint32_t fn_min;        // lower bound on the keys of live FN entries
-    uint32_t ff_min;        // lower bound on the keys of live FF entries
-    int32_t err;            // first dsssp_status != OK
-    uint32_t pad0;
+    uint32_t count;         // entries of the list this phase reads
+    uint32_t arcs;          // arcs of that list (LIGHT / HEAVY)
+    uint32_t pad[6];
+};
+
+// State only the serial step reads and writes.
+struct alignas(16) SerialState {
+    uint32_t mode, cur, scur, far_cur, qstamp, sround, T, pad0;
+    int64_t bucket;
     int64_t phases;
     uint64_t t_last;        // %globaltimer at the previous barrier
     uint64_t t_start;
     long long st[16];
 };
 
+struct Ctl {
+    // barrier words, alone on their line
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int32_t err;            // first dsssp_status != OK
+    uint32_t pad0[29];
+    PhaseDesc desc;
+    // counters updated with atomics during a phase: (entries << 32) | arcs
+    unsigned long long ctrF[2];
+    unsigned long long ctrS[2];
+    uint32_t nFar[2];
+    uint32_t far_min;       // lower bound on the keys of live far-pile entries
+    uint32_t pad1[9];
+    SerialState ss;
+};
+
 enum StatIdx {
     ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_SELECT = 3, ST_VLIGHT = 4, ST_VHEAVY = 5,
     ST_ALIGHT = 6, ST_AHEAVY = 7, ST_FARSCAN = 8, ST_IMPROVE = 9, ST_NSLIGHT = 10, ST_NSHEAVY = 11,
-    ST_NSSELECT = 12, ST_NSTOTAL = 13, ST_FFSCANS = 14
+    ST_NSSELECT = 12, ST_NSTOTAL = 13
 };
 
 // Per-vertex arc segments of the split layout: [x, y) light, [y, z) heavy.
@@ -158,12 +169,11 @@ struct SolveArgs {
     const uint2 *arcs;              // m: (head, weight bits), light-first per row
     unsigned long long *packed;     // n
     uint32_t *near_stamp;           // n
-    uint32_t *far_flag;             // n
+    uint32_t *far_flag;             // n: 0 no entry, 1 live entry, 2 stale entry
     uint32_t *s_stamp;              // n
     uint4 *F0, *F1;                 // n each
     uint4 *S0, *S1;                 // n each
-    uint32_t *FN0, *FN1;            // n each
-    uint32_t *FF0, *FF1;            // n each
+    uint32_t *FAR0, *FAR1;          // n each
     Ctl *ctl;
     double delta;
     int64_t timeout_ns;
@@ -172,7 +182,6 @@ struct SolveArgs {
     uint32_t m;
     uint32_t src;
     uint32_t inf_key;
-    uint32_t far_window;            // buckets covered by FN
     int32_t dtype;
     int32_t test_hook;
     uint32_t nblocks;

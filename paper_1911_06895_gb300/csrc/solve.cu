@@ -14,7 +14,7 @@
 // A vertex whose distance strictly decreases into bucket <= i is queued once
 // per phase: its light segment goes to the next F and, once per bucket, its
 // heavy segment to S (S = S u t_Bi, Fig. 1). A decrease into a later bucket
-// puts it on the far pile (two levels, see dsssp_internal.cuh).
+// puts it on the far pile.
 //
 // Load balance: F and S entries carry their arc offset within the list, so a
 // phase splits the list's flattened arcs into equal contiguous slices, one per
@@ -38,7 +38,7 @@ constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 constexpr int kIlp = 4;                // independent 32-arc steps per warp iteration
 constexpr uint32_t kMinSlice = 32u * kIlp;
 
-enum FarFlag : uint32_t { FAR_NONE = 0, FAR_FN = 1, FAR_FN_STALE = 2, FAR_FF = 3, FAR_FF_STALE = 4 };
+enum FarFlag : uint32_t { FAR_NONE = 0, FAR_LIVE = 1, FAR_STALE = 2 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -80,8 +80,7 @@ __device__ __forceinline__ constexpr uint32_t inf_key() {
 struct WarpStage {
     uint32_t fv[64], fd[64], fb[64];     // next-frontier entries (vertex, light degree, begin)
     uint32_t sv[64], sd[64], sb[64];     // S entries (vertex, heavy degree, begin)
-    uint32_t fn[64];                     // far pile, near level
-    uint32_t ff[64];                     // far pile, outer level
+    uint32_t far[64];                    // far-pile entries
 };
 
 // Write n <= 32 staged segment entries (lanes < n) to an F or S list.
@@ -157,25 +156,15 @@ __device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, ui
 }
 
 // ---------------------------------------------------------------------------
-// Per-phase constants every block reads from the control block after a barrier.
-struct Desc {
-    uint32_t mode, cur, scur, fn_cur, ff_cur, rescan_ff, qstamp, sround, T, Tw;
-    uint32_t spush;       // S list receiving pushes in this phase
-    uint32_t sstamp;      // S stamp of those pushes
-    uint32_t count;       // entries of the list this phase reads (SELECT: FN part)
-    uint32_t count2;      // SELECT: FF entries re-examined
-    uint32_t arcs;        // arcs of the list (LIGHT / HEAVY)
-};
-
 // Block-local accumulators flushed to the control block.
 struct BlockAcc {
-    uint32_t fn_min, ff_min;
+    uint32_t far_min;
     unsigned long long arcs_light, arcs_heavy, improvements, far_scanned;
 };
 
 // Pending pushes of one lane in one step.
 struct Push {
-    bool f, s, fn, ff;
+    bool f, s, far;
     uint32_t fdeg, fbeg, sdeg, sbeg;
 };
 
@@ -185,51 +174,47 @@ struct PushCtx {
     unsigned long long *ctrF;
     uint4 *S;
     unsigned long long *ctrS;
-    uint32_t *FN, *nFN, *FF, *nFF;
-    uint32_t nf, ns, nfn, nff;
+    uint32_t *FAR, *nFar;
+    uint32_t nf, ns, nfar;
 };
 
-// far pushes of LIGHT/HEAVY extend the current far lists; SELECT writes the next ones
-__device__ __forceinline__ PushCtx push_ctx(const SolveArgs &a, const Desc &d, bool select) {
+// LIGHT/HEAVY append to the current far list; SELECT rebuilds it into the other one
+__device__ __forceinline__ PushCtx push_ctx(const SolveArgs &a, const PhaseDesc &d, bool select) {
     Ctl *c = a.ctl;
     PushCtx q;
     q.F = d.cur ? a.F0 : a.F1;
     q.ctrF = &c->ctrF[d.cur ^ 1u];
     q.S = d.spush ? a.S1 : a.S0;
     q.ctrS = &c->ctrS[d.spush];
-    const uint32_t fn = select ? d.fn_cur ^ 1u : d.fn_cur;
-    const uint32_t ff = (select && d.rescan_ff) ? d.ff_cur ^ 1u : d.ff_cur;
-    q.FN = fn ? a.FN1 : a.FN0;
-    q.nFN = &c->nFN[fn];
-    q.FF = ff ? a.FF1 : a.FF0;
-    q.nFF = &c->nFF[ff];
-    q.nf = q.ns = q.nfn = q.nff = 0u;
+    const uint32_t fl = select ? d.far_cur ^ 1u : d.far_cur;
+    q.FAR = fl ? a.FAR1 : a.FAR0;
+    q.nFar = &c->nFar[fl];
+    q.nf = q.ns = q.nfar = 0u;
     return q;
 }
 
 __device__ __forceinline__ void stage_pushes(PushCtx &q, WarpStage &ws, const Push &p, uint32_t v) {
-    if (__ballot_sync(FULL, p.f || p.s || p.fn || p.ff) == 0u) return;
+    if (__ballot_sync(FULL, p.f || p.s || p.far) == 0u) return;
     stage_seg(p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
     stage_seg(p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-    stage_id(p.fn, v, ws.fn, q.nfn, q.FN, q.nFN);
-    stage_id(p.ff, v, ws.ff, q.nff, q.FF, q.nFF);
+    stage_id(p.far, v, ws.far, q.nfar, q.FAR, q.nFar);
 }
 
 // Flush the partially filled staging buffers (end of a phase).
 __device__ __forceinline__ void drain_pushes(PushCtx &q, WarpStage &ws) {
     if (q.nf) flush_seg(ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
     if (q.ns) flush_seg(ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-    if (q.nfn) flush_ids(ws.fn, q.nfn, q.FN, q.nFN);
-    if (q.nff) flush_ids(ws.ff, q.nff, q.FF, q.nFF);
+    if (q.nfar) flush_ids(ws.far, q.nfar, q.FAR, q.nFar);
     __syncwarp();
-    q.nf = q.ns = q.nfn = q.nff = 0u;
+    q.nf = q.ns = q.nfar = 0u;
 }
 
 // Queue v for bucket i (its key is now below T): once per phase into the next
 // F (its light segment), once per bucket into S (its heavy segment). A live
 // far-pile entry of v becomes stale. The loads are issued together with the
 // stamp exchange; they are simply unused when v is already queued.
-__device__ __forceinline__ void queue_near(const SolveArgs &a, const Desc &d, uint32_t v, Push &p, bool mark_far) {
+__device__ __forceinline__ void queue_near(const SolveArgs &a, const PhaseDesc &d, uint32_t v, Push &p,
+                                           bool mark_far) {
     const uint32_t prev = atomicExch(a.near_stamp + v, d.qstamp);
     const uint4 vi = a.vinfo[v];
     const uint32_t ss = __ldcg(a.s_stamp + v);
@@ -244,35 +229,26 @@ __device__ __forceinline__ void queue_near(const SolveArgs &a, const Desc &d, ui
         p.sbeg = vi.y;
         p.s = p.sdeg != 0u;
     }
-    if (ff == FAR_FN || ff == FAR_FF) a.far_flag[v] = ff + 1u;
+    if (ff == FAR_LIVE) a.far_flag[v] = FAR_STALE;
 }
 
 // relax(v, new_dist) of Section III-C, after the packed atomicMin found a strict
 // decrease of t[v]: v re-enters bucket i ((t_Req < t) o t_Bi) or goes to the far pile.
 template <int DT>
-__device__ __forceinline__ void on_improved(const SolveArgs &a, const Desc &d, uint32_t v, uint32_t ckey,
-                                            Push &p, uint32_t &fn_min, uint32_t &ff_min, uint32_t &improved) {
+__device__ __forceinline__ void on_improved(const SolveArgs &a, const PhaseDesc &d, uint32_t v, uint32_t ckey,
+                                            Push &p, uint32_t &far_min, uint32_t &improved) {
     ++improved;
     if (ckey < d.T) {
         queue_near(a, d, v, p, true);
-        return;
+    } else {
+        far_min = min(far_min, ckey);
+        p.far = atomicExch(a.far_flag + v, FAR_LIVE) == FAR_NONE;
     }
-    const uint32_t want = ckey < d.Tw ? FAR_FN : FAR_FF;
-    uint32_t old = atomicCAS(a.far_flag + v, FAR_NONE, want);
-    if (old == FAR_NONE) {
-        old = want;
-        if (want == FAR_FN) p.fn = true; else p.ff = true;
-    } else if (old == FAR_FN_STALE || old == FAR_FF_STALE) {
-        // cannot happen for a settled vertex; revive the existing entry to stay safe
-        atomicCAS(a.far_flag + v, old, old - 1u);
-        old -= 1u;
-    }
-    if (old == FAR_FN) fn_min = min(fn_min, ckey); else ff_min = min(ff_min, ckey);
 }
 
 // LIGHT / HEAVY: relax the arcs of a list, split evenly over the warps.
 template <int DT, bool LIGHT>
-__device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot, WarpStage *stage) {
+__device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot, WarpStage *stage) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw_all = (gridDim.x * blockDim.x) >> 5;
@@ -283,7 +259,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
     // at least kMinSlice arcs per warp: small phases use few warps
     const uint32_t want_w = (E + kMinSlice - 1u) / kMinSlice;
     const uint32_t nw = want_w < nw_all ? want_w : nw_all;
-    uint32_t fn_min = inf_key<DT>(), ff_min = inf_key<DT>();
+    uint32_t far_min = inf_key<DT>();
     uint32_t improved = 0;
     if (gw < nw) {
         const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
@@ -393,7 +369,7 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
                 Push p{};
                 const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
                 if (cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k])      // strict distance decrease
-                    on_improved<DT>(a, d, arc[k].x, ck[k], p, fn_min, ff_min, improved);
+                    on_improved<DT>(a, d, arc[k].x, ck[k], p, far_min, improved);
                 stage_pushes(q, ws, p, arc[k].x);
             }
         }
@@ -403,194 +379,202 @@ __device__ void phase_arcs(const SolveArgs &a, const Desc &d, BlockAcc &acc, int
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
         }
     }
-    if (fn_min < inf_key<DT>()) atomicMin(&acc.fn_min, fn_min);
-    if (ff_min < inf_key<DT>()) atomicMin(&acc.ff_min, ff_min);
+    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
     if (improved) atomicAdd(&acc.improvements, (unsigned long long)improved);
 }
 
 // SELECT: compact the far pile. Live entries whose key is below T (bucket <= i)
-// are queued into F and S; the rest stay (FF entries below the new window move
-// to FN), and their minimum keys bound the next bucket; stale entries are dropped.
+// are queued into F and S; the rest stay, and their minimum key bounds the next
+// bucket; stale entries are dropped. Each lane examines kIlp entries at once.
 template <int DT>
-__device__ void phase_select(const SolveArgs &a, const Desc &d, BlockAcc &acc, WarpStage *stage) {
+__device__ void phase_select(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, WarpStage *stage) {
     const uint32_t lane = lane_id();
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t *fn_in = d.fn_cur ? a.FN1 : a.FN0;
-    const uint32_t *ff_in = d.ff_cur ? a.FF1 : a.FF0;
-    const uint32_t nfn = d.count, total = d.count + d.count2;
-    uint32_t fn_min = inf_key<DT>(), ff_min = inf_key<DT>();
+    const uint32_t *in = d.far_cur ? a.FAR1 : a.FAR0;
+    const uint32_t count = d.count;
+    uint32_t far_min = inf_key<DT>();
     PushCtx q = push_ctx(a, d, true);
     WarpStage &ws = stage[threadIdx.x >> 5];
-    for (unsigned long long base = (unsigned long long)gw * 32u; base < total; base += (unsigned long long)nw * 32u) {
-        const uint32_t idx = (uint32_t)base + lane;
-        Push p{};
-        uint32_t v = 0;
-        if (idx < total) {
-            const bool from_fn = idx < nfn;
-            v = from_fn ? __ldcs(fn_in + idx) : __ldcs(ff_in + (idx - nfn));
-            const uint32_t live = from_fn ? FAR_FN : FAR_FF;
-            const uint32_t f = v < a.n ? __ldcg(a.far_flag + v) : FAR_NONE;
-            if (v < a.n && f == live) {
-                const uint32_t k = (uint32_t)(__ldcg(a.packed + v) >> 32);
-                if (k < d.T) {
-                    a.far_flag[v] = FAR_NONE;
-                    queue_near(a, d, v, p, false);
-                } else if (from_fn || k < d.Tw) {
-                    if (!from_fn) a.far_flag[v] = FAR_FN;
-                    p.fn = true;
-                    fn_min = min(fn_min, k);
-                } else {
-                    p.ff = true;
-                    ff_min = min(ff_min, k);
-                }
-            } else if (v < a.n && f == live + 1u) {
-                a.far_flag[v] = FAR_NONE;          // stale entry dropped
-            }
+    const unsigned long long stride = (unsigned long long)nw * 32u * kIlp;
+    for (unsigned long long base = (unsigned long long)gw * 32u * kIlp; base < count; base += stride) {
+        uint32_t v[kIlp], f[kIlp], k[kIlp];
+        #pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            const unsigned long long idx = base + 32u * j + lane;
+            v[j] = idx < count ? __ldcs(in + idx) : 0xFFFFFFFFu;
         }
-        stage_pushes(q, ws, p, v);
+        #pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            f[j] = v[j] < a.n ? __ldcg(a.far_flag + v[j]) : FAR_NONE;
+            k[j] = v[j] < a.n ? (uint32_t)(__ldcg(a.packed + v[j]) >> 32) : inf_key<DT>();
+        }
+        #pragma unroll
+        for (int j = 0; j < kIlp; ++j) {
+            Push p{};
+            if (f[j] == FAR_LIVE) {
+                if (k[j] < d.T) {
+                    a.far_flag[v[j]] = FAR_NONE;
+                    queue_near(a, d, v[j], p, false);
+                } else {
+                    p.far = true;                      // stays on the (rebuilt) far pile
+                    far_min = min(far_min, k[j]);
+                }
+            } else if (f[j] == FAR_STALE) {
+                a.far_flag[v[j]] = FAR_NONE;          // stale entry dropped
+            }
+            stage_pushes(q, ws, p, v[j]);
+        }
     }
     drain_pushes(q, ws);
-    if (fn_min < inf_key<DT>()) atomicMin(&acc.fn_min, fn_min);
-    if (ff_min < inf_key<DT>()) atomicMin(&acc.ff_min, ff_min);
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&acc.far_scanned, (unsigned long long)total);
+    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
+    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&acc.far_scanned, (unsigned long long)count);
 }
 
 // ---------------------------------------------------------------------------
 // Serial step: runs on one thread after every block has finished a phase.
-// Decides the next phase (the control flow of Fig. 1) and resets consumed lists.
+// Loads the serial state and the list counters in one batch, decides the next
+// phase (the control flow of Fig. 1) in registers, resets consumed counters
+// and publishes the next PhaseDesc.
 template <int DT>
 __device__ void serial_step(const SolveArgs &a) {
     Ctl *c = a.ctl;
+    SerialState s;
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&c->ss);
+        uint4 *dst = reinterpret_cast<uint4 *>(&s);
+        #pragma unroll
+        for (int k = 0; k < (int)(sizeof(SerialState) / 16); ++k) dst[k] = __ldcg(src + k);
+    }
+    const unsigned long long cf0 = __ldcg(&c->ctrF[0]), cf1 = __ldcg(&c->ctrF[1]);
+    const unsigned long long cs0 = __ldcg(&c->ctrS[0]), cs1 = __ldcg(&c->ctrS[1]);
+    const uint32_t nfar0 = __ldcg(&c->nFar[0]), nfar1 = __ldcg(&c->nFar[1]);
+    const uint32_t far_min = __ldcg(&c->far_min);
     const uint64_t now = globaltimer();
-    const uint64_t dt = now - c->t_last;
-    c->t_last = now;
-    const uint32_t mode = c->mode;
-    if (mode == MODE_LIGHT) c->st[ST_NSLIGHT] += (long long)dt;
-    else if (mode == MODE_HEAVY) c->st[ST_NSHEAVY] += (long long)dt;
-    else if (mode == MODE_SELECT) c->st[ST_NSSELECT] += (long long)dt;
-    c->phases += 1;
-    if (c->phases >= a.max_phases) {
+    const uint64_t dt = now - s.t_last;
+    s.t_last = now;
+    unsigned long long ctrF[2] = {cf0, cf1}, ctrS[2] = {cs0, cs1};
+    uint32_t nFar[2] = {nfar0, nfar1};
+    bool resetF = false, resetS = false, resetFar = false;   // consumed list counters
+    uint32_t rF = 0, rS = 0, rFar = 0;
+    const uint32_t mode = s.mode;
+    PhaseDesc nd{};
+    if (mode == MODE_LIGHT) s.st[ST_NSLIGHT] += (long long)dt;
+    else if (mode == MODE_HEAVY) s.st[ST_NSHEAVY] += (long long)dt;
+    else if (mode == MODE_SELECT) s.st[ST_NSSELECT] += (long long)dt;
+    s.phases += 1;
+    bool done = false;
+    if (s.phases >= a.max_phases) {
         atomicCAS(&c->err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
-        c->mode = MODE_DONE;
-        return;
-    }
-    switch (mode) {
-    case MODE_LIGHT:
-        c->st[ST_LIGHT] += 1;
-        c->st[ST_VLIGHT] += (long long)(c->ctrF[c->cur] >> 32);
-        c->ctrF[c->cur] = 0ull;
-        break;
-    case MODE_HEAVY:
-        c->st[ST_HEAVY] += 1;
-        c->st[ST_VHEAVY] += (long long)(c->ctrS[c->scur] >> 32);
-        c->ctrS[c->scur] = 0ull;
-        c->scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
-        c->sround += 1u;
-        break;
-    case MODE_SELECT:
-        c->st[ST_SELECT] += 1;
-        c->nFN[c->fn_cur] = 0u;
-        c->fn_cur ^= 1u;
-        if (c->rescan_ff) {
-            c->st[ST_FFSCANS] += 1;
-            c->nFF[c->ff_cur] = 0u;
-            c->ff_cur ^= 1u;
-        }
-        break;
-    default:
-        return;
-    }
-    c->qstamp += 1u;                           // every phase queues under a fresh stamp
-    const uint32_t nxt = c->cur ^ 1u;
-    if ((c->ctrF[nxt] >> 32) != 0ull) {        // inner loop of Fig. 1: while t_Bi != 0
-        if (mode == MODE_SELECT) c->st[ST_BUCKETS] += 1;
-        c->cur = nxt;
-        c->mode = MODE_LIGHT;
-        return;
-    }
-    if ((c->ctrS[c->scur] >> 32) != 0ull) {    // bucket settled: heavy pass over S
-        if (mode == MODE_SELECT) c->st[ST_BUCKETS] += 1;
-        c->mode = MODE_HEAVY;
-        return;
-    }
-    // next non-empty bucket
-    const uint32_t fm = min(c->fn_min, c->ff_min);
-    if (fm >= inf_key<DT>()) {
-        if (c->nFN[c->fn_cur] == 0u && c->nFF[c->ff_cur] == 0u) {
-            c->mode = MODE_DONE;
-            c->st[ST_NSTOTAL] = (long long)(now - c->t_start);
-            return;
-        }
-        c->T = 0u;                              // only stale entries remain: drop them
-        c->Tw = 0u;
-        c->rescan_ff = c->nFF[c->ff_cur] != 0u;
+        done = true;
     } else {
-        const int64_t i = bucket_of_key(fm, DT, a.delta);
-        c->bucket = i;
-        c->T = i < INT64_MAX ? bucket_floor_key(i + 1, DT, a.delta) : 0u;
-        if (c->T <= fm) c->T = fm + 1u;         // always take the smallest live key
-        c->rescan_ff = c->ff_min < c->T;
-        if (c->rescan_ff) {
-            const int64_t w = (int64_t)a.far_window;
-            c->Tw = i < INT64_MAX - w ? bucket_floor_key(i + w, DT, a.delta) : inf_key<DT>();
-            if (c->Tw < c->T) c->Tw = c->T;
+        switch (mode) {
+        case MODE_LIGHT:
+            s.st[ST_LIGHT] += 1;
+            s.st[ST_VLIGHT] += (long long)(ctrF[s.cur] >> 32);
+            resetF = true; rF = s.cur; ctrF[s.cur] = 0ull;
+            break;
+        case MODE_HEAVY:
+            s.st[ST_HEAVY] += 1;
+            s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
+            resetS = true; rS = s.scur; ctrS[s.scur] = 0ull;
+            s.scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
+            s.sround += 1u;
+            break;
+        case MODE_SELECT:
+            s.st[ST_SELECT] += 1;
+            resetFar = true; rFar = s.far_cur; nFar[s.far_cur] = 0u;
+            s.far_cur ^= 1u;
+            break;
+        default:
+            done = true;
+            break;
         }
     }
-    c->fn_min = inf_key<DT>();
-    if (c->rescan_ff) c->ff_min = inf_key<DT>();
-    c->mode = MODE_SELECT;
+    uint32_t next_mode = MODE_DONE;
+    bool reset_min = false;
+    if (!done) {
+        s.qstamp += 1u;                            // every phase queues under a fresh stamp
+        const uint32_t nxt = s.cur ^ 1u;
+        if ((ctrF[nxt] >> 32) != 0ull) {           // inner loop of Fig. 1: while t_Bi != 0
+            if (mode == MODE_SELECT) s.st[ST_BUCKETS] += 1;
+            s.cur = nxt;
+            next_mode = MODE_LIGHT;
+        } else if ((ctrS[s.scur] >> 32) != 0ull) { // bucket settled: heavy pass over S
+            if (mode == MODE_SELECT) s.st[ST_BUCKETS] += 1;
+            next_mode = MODE_HEAVY;
+        } else if (far_min >= inf_key<DT>() && nFar[s.far_cur] == 0u) {
+            next_mode = MODE_DONE;                 // nothing left in any bucket
+        } else {                                   // next non-empty bucket
+            if (far_min >= inf_key<DT>()) {
+                s.T = 0u;                          // only stale entries remain: drop them
+            } else {
+                const int64_t i = bucket_of_key(far_min, DT, a.delta);
+                s.bucket = i;
+                s.T = i < INT64_MAX ? bucket_floor_key(i + 1, DT, a.delta) : 0u;
+                if (s.T <= far_min) s.T = far_min + 1u;     // always take the smallest live key
+            }
+            reset_min = true;
+            next_mode = MODE_SELECT;
+        }
+    }
+    if (next_mode == MODE_DONE) s.st[ST_NSTOTAL] = (long long)(now - s.t_start);
+    s.mode = next_mode;
+    nd.mode = next_mode;
+    nd.cur = s.cur;
+    nd.scur = s.scur;
+    // S pushes: into the current S, except during a heavy pass, which feeds the next one
+    nd.spush = next_mode == MODE_HEAVY ? s.scur ^ 1u : s.scur;
+    nd.sstamp = next_mode == MODE_HEAVY ? s.sround + 1u : s.sround;
+    nd.far_cur = s.far_cur;
+    nd.qstamp = s.qstamp;
+    nd.T = s.T;
+    if (next_mode == MODE_LIGHT) { nd.count = (uint32_t)(ctrF[s.cur] >> 32); nd.arcs = (uint32_t)ctrF[s.cur]; }
+    else if (next_mode == MODE_HEAVY) { nd.count = (uint32_t)(ctrS[s.scur] >> 32); nd.arcs = (uint32_t)ctrS[s.scur]; }
+    else if (next_mode == MODE_SELECT) nd.count = nFar[s.far_cur];
+    // write back: consumed counters, serial state, descriptor
+    if (resetF) c->ctrF[rF] = 0ull;
+    if (resetS) c->ctrS[rS] = 0ull;
+    if (resetFar) c->nFar[rFar] = 0u;
+    if (reset_min) c->far_min = inf_key<DT>();
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(&s);
+        uint4 *dst = reinterpret_cast<uint4 *>(&c->ss);
+        #pragma unroll
+        for (int k = 0; k < (int)(sizeof(SerialState) / 16); ++k) dst[k] = src[k];
+        const uint4 *ds = reinterpret_cast<const uint4 *>(&nd);
+        uint4 *dd = reinterpret_cast<uint4 *>(&c->desc);
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) dd[k] = ds[k];
+    }
 }
 
-__device__ __forceinline__ void read_desc(const Ctl *c, Desc &d) {
-    d.mode = vload(&c->mode);
-    d.cur = vload(&c->cur);
-    d.scur = vload(&c->scur);
-    d.fn_cur = vload(&c->fn_cur);
-    d.ff_cur = vload(&c->ff_cur);
-    d.rescan_ff = vload(&c->rescan_ff);
-    d.qstamp = vload(&c->qstamp);
-    d.sround = vload(&c->sround);
-    d.T = vload(&c->T);
-    d.Tw = vload(&c->Tw);
-    // S pushes: into the current S, except during a heavy pass, which feeds the next one
-    d.spush = d.mode == MODE_HEAVY ? d.scur ^ 1u : d.scur;
-    d.sstamp = d.mode == MODE_HEAVY ? d.sround + 1u : d.sround;
-    d.count = 0;
-    d.count2 = 0;
-    d.arcs = 0;
-    unsigned long long ctr = 0;
-    switch (d.mode) {
-    case MODE_LIGHT: ctr = vload(&c->ctrF[d.cur]); break;
-    case MODE_HEAVY: ctr = vload(&c->ctrS[d.scur]); break;
-    case MODE_SELECT:
-        d.count = vload(&c->nFN[d.fn_cur]);
-        d.count2 = d.rescan_ff ? vload(&c->nFF[d.ff_cur]) : 0u;
-        break;
-    default: break;
-    }
-    if (d.mode == MODE_LIGHT || d.mode == MODE_HEAVY) {
-        d.count = (uint32_t)(ctr >> 32);
-        d.arcs = (uint32_t)ctr;
-    }
+__device__ __forceinline__ void read_desc(const Ctl *c, PhaseDesc &d) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(&c->desc);
+    uint4 *dst = reinterpret_cast<uint4 *>(&d);
+    #pragma unroll
+    for (int k = 0; k < 4; ++k) dst[k] = __ldcg(src + k);
 }
 
 __device__ __forceinline__ void flush_far_min(Ctl *c, BlockAcc &acc, uint32_t inf) {
-    if (acc.fn_min < inf) { atomicMin(&c->fn_min, acc.fn_min); acc.fn_min = inf; }
-    if (acc.ff_min < inf) { atomicMin(&c->ff_min, acc.ff_min); acc.ff_min = inf; }
+    if (acc.far_min < inf) {
+        atomicMin(&c->far_min, acc.far_min);
+        acc.far_min = inf;
+    }
 }
 
 __device__ __forceinline__ void flush_stats(Ctl *c, BlockAcc &acc) {
-    if (acc.arcs_light) atomicAdd((unsigned long long *)&c->st[ST_ALIGHT], acc.arcs_light);
-    if (acc.arcs_heavy) atomicAdd((unsigned long long *)&c->st[ST_AHEAVY], acc.arcs_heavy);
-    if (acc.improvements) atomicAdd((unsigned long long *)&c->st[ST_IMPROVE], acc.improvements);
-    if (acc.far_scanned) atomicAdd((unsigned long long *)&c->st[ST_FARSCAN], acc.far_scanned);
+    long long *st = c->ss.st;
+    if (acc.arcs_light) atomicAdd((unsigned long long *)&st[ST_ALIGHT], acc.arcs_light);
+    if (acc.arcs_heavy) atomicAdd((unsigned long long *)&st[ST_AHEAVY], acc.arcs_heavy);
+    if (acc.improvements) atomicAdd((unsigned long long *)&st[ST_IMPROVE], acc.improvements);
+    if (acc.far_scanned) atomicAdd((unsigned long long *)&st[ST_FARSCAN], acc.far_scanned);
     acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
 }
 
 template <int DT>
 __device__ __forceinline__ void acc_init(BlockAcc &acc) {
-    acc.fn_min = acc.ff_min = inf_key<DT>();
+    acc.far_min = inf_key<DT>();
     acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
 }
 
@@ -622,14 +606,14 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
             }
             __threadfence();
         }
-        *s_ok = (vload(&c->err) == 0) && (vload(&c->mode) != MODE_DONE);
+        *s_ok = vload(&c->err) == 0;
     }
     __syncthreads();
     return *s_ok != 0;
 }
 
 template <int DT>
-__device__ __forceinline__ void run_phase(const SolveArgs &a, const Desc &d, BlockAcc &acc, int *slot,
+__device__ __forceinline__ void run_phase(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot,
                                           WarpStage *stage) {
     switch (d.mode) {
     case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot, stage); break;
@@ -643,7 +627,7 @@ template <int DT>
 __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
     __shared__ WarpStage stage[kMaxWarps];
-    __shared__ Desc s_desc;
+    __shared__ PhaseDesc s_desc;
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
     if (a.test_hook == DSSSP_HOOK_STALL_BARRIER && blockIdx.x == 1) return;
@@ -651,7 +635,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     for (;;) {
         if (threadIdx.x == 0) read_desc(a.ctl, s_desc);
         __syncthreads();
-        const Desc d = s_desc;
+        const PhaseDesc &d = s_desc;
         if (d.mode == MODE_DONE) break;
         run_phase<DT>(a, d, acc, slot, stage);
         if (!grid_barrier<DT>(a, acc, &s_ok)) break;
@@ -665,14 +649,14 @@ template <int DT, uint32_t MODE>
 __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
     __shared__ WarpStage stage[kMaxWarps];
-    __shared__ Desc s_desc;
+    __shared__ PhaseDesc s_desc;
     __shared__ BlockAcc acc;
     if (threadIdx.x == 0) {
         read_desc(a.ctl, s_desc);
         acc_init<DT>(acc);
     }
     __syncthreads();
-    const Desc d = s_desc;
+    const PhaseDesc &d = s_desc;
     if (d.mode != MODE) return;
     run_phase<DT>(a, d, acc, slot, stage);
     __syncthreads();
@@ -684,7 +668,7 @@ __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
 
 template <int DT>
 __global__ void k_serial(SolveArgs a) {
-    if (vload(&a.ctl->mode) != MODE_DONE) serial_step<DT>(a);
+    if (vload(&a.ctl->desc.mode) != MODE_DONE) serial_step<DT>(a);
 }
 
 // ---- init / unpack -------------------------------------------------------------
@@ -704,30 +688,29 @@ __global__ void k_init(SolveArgs a) {
         const uint4 vs = a.vinfo[a.src];
         c->bar_count = 0u;
         c->bar_gen = 0u;
-        c->mode = MODE_LIGHT;     // B_0 = {s}
-        c->cur = 0u;
-        c->scur = 0u;
-        c->fn_cur = 0u;
-        c->ff_cur = 0u;
-        c->rescan_ff = 0u;
-        c->qstamp = 1u;
-        c->sround = 1u;
-        c->bucket = 0;
-        c->T = bucket_floor_key(1, DT, a.delta);
-        c->Tw = bucket_floor_key((int64_t)a.far_window, DT, a.delta);
-        if (c->Tw < c->T) c->Tw = c->T;
+        c->err = 0;
+        SerialState s{};
+        s.mode = MODE_LIGHT;      // B_0 = {s}
+        s.qstamp = 1u;
+        s.sround = 1u;
+        s.T = bucket_floor_key(1, DT, a.delta);
+        s.st[ST_BUCKETS] = 1;
+        s.t_start = s.t_last = globaltimer();
+        c->ss = s;
         c->ctrF[0] = (vs.y > vs.x) ? ((1ull << 32) | (vs.y - vs.x)) : 0ull;
         c->ctrF[1] = 0ull;
         c->ctrS[0] = (vs.z > vs.y) ? ((1ull << 32) | (vs.z - vs.y)) : 0ull;
         c->ctrS[1] = 0ull;
-        c->nFN[0] = c->nFN[1] = 0u;
-        c->nFF[0] = c->nFF[1] = 0u;
-        c->fn_min = c->ff_min = inf_key<DT>();
-        c->err = 0;
-        c->phases = 0;
-        for (int k = 0; k < 16; ++k) c->st[k] = 0;
-        c->st[ST_BUCKETS] = 1;
-        c->t_start = c->t_last = globaltimer();
+        c->nFar[0] = c->nFar[1] = 0u;
+        c->far_min = inf_key<DT>();
+        PhaseDesc d{};
+        d.mode = MODE_LIGHT;
+        d.qstamp = 1u;
+        d.sstamp = 1u;
+        d.T = s.T;
+        d.count = (uint32_t)(c->ctrF[0] >> 32);
+        d.arcs = (uint32_t)c->ctrF[0];
+        c->desc = d;
         a.F0[0] = make_uint4(a.src, 0u, vs.x, 0u);
         a.S0[0] = make_uint4(a.src, 0u, vs.y, 0u);
     }

@@ -46,7 +46,7 @@ DSSSP_HOOK_STALL_BARRIER = 1
 
 class dsssp_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("mode", ctypes.c_int32),
-                ("block_size", ctypes.c_int32), ("grid_size", ctypes.c_int32), ("far_window", ctypes.c_int32),
+                ("block_size", ctypes.c_int32), ("grid_size", ctypes.c_int32), ("reserved0", ctypes.c_int32),
                 ("max_phases", ctypes.c_int64), ("timeout_ns", ctypes.c_int64), ("test_hook", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 5)]
 
@@ -55,7 +55,7 @@ class dsssp_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "buckets", "light_phases", "heavy_phases", "select_phases", "vertices_light",
         "vertices_heavy", "arcs_light", "arcs_heavy", "far_scanned", "improvements", "ns_light",
-        "ns_heavy", "ns_select", "ns_total", "far_rescans", "grid_size", "block_size")] + [("reserved", ctypes.c_int64 * 7)]
+        "ns_heavy", "ns_select", "ns_total", "grid_size", "block_size")] + [("reserved", ctypes.c_int64 * 8)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
