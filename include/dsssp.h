@@ -109,9 +109,11 @@ typedef struct {
     int64_t ns_heavy;         /* device time in heavy passes                                    */
     int64_t ns_select;        /* device time in next-bucket searches                           */
     int64_t ns_total;         /* device time of the whole solve kernel                          */
+    int64_t ns_first_arrival; /* sum over phases: phase start to the first block's barrier arrival */
+    int64_t ns_arrival_spread;/* sum over phases: first to last barrier arrival                  */
     int64_t grid_size;        /* blocks used                                                    */
     int64_t block_size;       /* threads per block used                                          */
-    int64_t reserved[8];
+    int64_t reserved[6];
 } dsssp_stats;
 
 /* Human-readable name of a status code (static string, never NULL). */

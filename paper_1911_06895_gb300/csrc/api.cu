@@ -186,6 +186,8 @@ void fill_stats(const Ctl &ctl, int grid, int block, dsssp_stats *s) {
     s->ns_heavy = st[ST_NSHEAVY];
     s->ns_select = st[ST_NSSELECT];
     s->ns_total = st[ST_NSTOTAL];
+    s->ns_first_arrival = st[ST_NSFIRST];
+    s->ns_arrival_spread = st[ST_NSSPREAD];
     s->grid_size = grid;
     s->block_size = block;
 }

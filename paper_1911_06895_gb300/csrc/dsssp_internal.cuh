@@ -151,14 +151,16 @@ struct Ctl {
     unsigned long long ctrS[2];
     uint32_t nFar[2];
     uint32_t far_min;       // lower bound on the keys of live far-pile entries
-    uint32_t pad1[9];
+    uint32_t pad1;
+    uint64_t t_first;       // %globaltimer of the first arrival at the current barrier
+    uint32_t pad2[6];
     SerialState ss;
 };
 
 enum StatIdx {
     ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_SELECT = 3, ST_VLIGHT = 4, ST_VHEAVY = 5,
     ST_ALIGHT = 6, ST_AHEAVY = 7, ST_FARSCAN = 8, ST_IMPROVE = 9, ST_NSLIGHT = 10, ST_NSHEAVY = 11,
-    ST_NSSELECT = 12, ST_NSTOTAL = 13
+    ST_NSSELECT = 12, ST_NSTOTAL = 13, ST_NSFIRST = 14, ST_NSSPREAD = 15
 };
 
 // Per-vertex arc segments of the split layout: [x, y) light, [y, z) heavy.

@@ -450,8 +450,13 @@ __device__ void serial_step(const SolveArgs &a) {
     const unsigned long long cs0 = __ldcg(&c->ctrS[0]), cs1 = __ldcg(&c->ctrS[1]);
     const uint32_t nfar0 = __ldcg(&c->nFar[0]), nfar1 = __ldcg(&c->nFar[1]);
     const uint32_t far_min = __ldcg(&c->far_min);
+    const uint64_t t_first = __ldcg(&c->t_first);
     const uint64_t now = globaltimer();
     const uint64_t dt = now - s.t_last;
+    if (t_first > s.t_last && t_first <= now) {      // persistent mode only
+        s.st[ST_NSFIRST] += (long long)(t_first - s.t_last);
+        s.st[ST_NSSPREAD] += (long long)(now - t_first);
+    }
     s.t_last = now;
     unsigned long long ctrF[2] = {cf0, cf1}, ctrS[2] = {cs0, cs1};
     uint32_t nFar[2] = {nfar0, nfar1};
@@ -589,6 +594,7 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
         __threadfence();
         const unsigned gen = vload(&c->bar_gen);
         const unsigned arrived = atomicAdd(&c->bar_count, 1u);
+        if (arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
         if (arrived == a.nblocks - 1u) {
             atomicExch(&c->bar_count, 0u);
             __threadfence();
