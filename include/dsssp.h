@@ -85,7 +85,9 @@ typedef struct {
     int32_t  mode;          /* dsssp_mode; default DSSSP_MODE_PERSISTENT                        */
     int32_t  block_size;    /* threads per block, multiple of 32, <= 512; default 512           */
     int32_t  grid_size;     /* blocks of the persistent kernel; default = all co-resident blocks */
-    int32_t  reserved0;     /* must be 0                                                         */
+    int32_t  solo_work;     /* phases with at most this many arcs (light/heavy) or far-pile
+                               entries (next-bucket search) run on one block without grid
+                               barriers; default 8192, -1 disables                              */
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */

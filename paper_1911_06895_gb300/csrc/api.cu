@@ -221,6 +221,7 @@ dsssp_status dsssp_options_default(dsssp_options *opt) {
     opt->grid_size = 0;
     opt->max_phases = (int64_t)1 << 26;
     opt->timeout_ns = 2000000000LL;
+    opt->solo_work = 8192;
     return DSSSP_OK;
 }
 
@@ -320,7 +321,7 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
         opt.mode = opt_in->mode;
         if (opt_in->block_size) opt.block_size = opt_in->block_size;
         if (opt_in->grid_size) opt.grid_size = opt_in->grid_size;
-        if (opt_in->reserved0) return DSSSP_ERR_INVALID_ARG;
+        if (opt_in->solo_work) opt.solo_work = opt_in->solo_work;
         if (opt_in->max_phases) opt.max_phases = opt_in->max_phases;
         if (opt_in->timeout_ns) opt.timeout_ns = opt_in->timeout_ns;
         opt.test_hook = opt_in->test_hook;
@@ -356,6 +357,8 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     a.max_phases = opt.max_phases;
     a.n = (uint32_t)g->n;
     a.m = (uint32_t)g->m;
+    // persistent mode only: the stepped mode has no grid barrier to save
+    a.solo_work = (opt.mode == DSSSP_MODE_PERSISTENT && opt.solo_work > 0) ? (uint32_t)opt.solo_work : 0u;
     a.src = (uint32_t)src;
     a.inf_key = key_inf(g->dtype);
     a.dtype = g->dtype;

@@ -126,7 +126,8 @@ struct alignas(64) PhaseDesc {
     uint32_t T;             // key < T  <=>  bucket <= i
     uint32_t count;         // entries of the list this phase reads
     uint32_t arcs;          // arcs of that list (LIGHT / HEAVY)
-    uint32_t pad[6];
+    uint32_t solo;          // 1: block 0 alone runs this phase (little work), the others wait
+    uint32_t pad[5];
 };
 
 // State only the serial step reads and writes.
@@ -184,6 +185,7 @@ struct SolveArgs {
     uint32_t m;
     uint32_t src;
     uint32_t inf_key;
+    uint32_t solo_work;             // phases with at most this many arcs / far entries run solo
     int32_t dtype;
     int32_t test_hook;
     uint32_t nblocks;

@@ -110,51 +110,6 @@ __device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32
     if (lane < n) list[base + lane] = bv[lane];
 }
 
-// Stage one (vertex, degree, begin) per pushing lane; flush 32 when full.
-__device__ __forceinline__ void stage_seg(bool pred, uint32_t v, uint32_t deg, uint32_t beg, uint32_t *bv,
-                                          uint32_t *bd, uint32_t *bb, uint32_t &cnt, uint4 *list,
-                                          unsigned long long *ctr) {
-    const uint32_t mask = __ballot_sync(FULL, pred);
-    if (mask == 0u) return;
-    const uint32_t lane = lane_id();
-    if (pred) {
-        const uint32_t k = cnt + __popc(mask & lanemask_lt());
-        bv[k] = v; bd[k] = deg; bb[k] = beg;
-    }
-    cnt += __popc(mask);
-    __syncwarp();
-    if (cnt >= 32u) {
-        flush_seg(bv, bd, bb, 32u, list, ctr);
-        const uint32_t rest = cnt - 32u;
-        uint32_t x = 0, y = 0, z = 0;
-        if (lane < rest) { x = bv[32 + lane]; y = bd[32 + lane]; z = bb[32 + lane]; }
-        __syncwarp();
-        if (lane < rest) { bv[lane] = x; bd[lane] = y; bb[lane] = z; }
-        __syncwarp();
-        cnt = rest;
-    }
-}
-
-__device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, uint32_t &cnt, uint32_t *list,
-                                         uint32_t *counter) {
-    const uint32_t mask = __ballot_sync(FULL, pred);
-    if (mask == 0u) return;
-    const uint32_t lane = lane_id();
-    if (pred) bv[cnt + __popc(mask & lanemask_lt())] = v;
-    cnt += __popc(mask);
-    __syncwarp();
-    if (cnt >= 32u) {
-        flush_ids(bv, 32u, list, counter);
-        const uint32_t rest = cnt - 32u;
-        uint32_t x = 0;
-        if (lane < rest) x = bv[32 + lane];
-        __syncwarp();
-        if (lane < rest) bv[lane] = x;
-        __syncwarp();
-        cnt = rest;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Block-local accumulators flushed to the control block.
 struct BlockAcc {
@@ -168,43 +123,92 @@ struct Push {
     uint32_t fdeg, fbeg, sdeg, sbeg;
 };
 
-// The lists a phase pushes into, and the warp's staged counts.
-struct PushCtx {
-    uint4 *F;
-    unsigned long long *ctrF;
-    uint4 *S;
-    unsigned long long *ctrS;
-    uint32_t *FAR, *nFar;
+// The warp's staged counts. The destination lists follow from the phase
+// descriptor (in shared memory) and are resolved only when a buffer is flushed,
+// so they do not hold registers in the relaxation loop. LIGHT/HEAVY append to
+// the current far list; SELECT rebuilds the far pile into the other one.
+struct PushCnt {
     uint32_t nf, ns, nfar;
 };
 
-// LIGHT/HEAVY append to the current far list; SELECT rebuilds it into the other one
-__device__ __forceinline__ PushCtx push_ctx(const SolveArgs &a, const PhaseDesc &d, bool select) {
-    Ctl *c = a.ctl;
-    PushCtx q;
-    q.F = d.cur ? a.F0 : a.F1;
-    q.ctrF = &c->ctrF[d.cur ^ 1u];
-    q.S = d.spush ? a.S1 : a.S0;
-    q.ctrS = &c->ctrS[d.spush];
-    const uint32_t fl = select ? d.far_cur ^ 1u : d.far_cur;
-    q.FAR = fl ? a.FAR1 : a.FAR0;
-    q.nFar = &c->nFar[fl];
-    q.nf = q.ns = q.nfar = 0u;
-    return q;
+__device__ __forceinline__ uint4 *dst_F(const SolveArgs &a, const PhaseDesc &d) { return d.cur ? a.F0 : a.F1; }
+__device__ __forceinline__ unsigned long long *ctr_F(const SolveArgs &a, const PhaseDesc &d) {
+    return &a.ctl->ctrF[d.cur ^ 1u];
+}
+__device__ __forceinline__ uint4 *dst_S(const SolveArgs &a, const PhaseDesc &d) { return d.spush ? a.S1 : a.S0; }
+__device__ __forceinline__ unsigned long long *ctr_S(const SolveArgs &a, const PhaseDesc &d) {
+    return &a.ctl->ctrS[d.spush];
+}
+__device__ __forceinline__ uint32_t far_list_index(const PhaseDesc &d) {
+    return d.mode == MODE_SELECT ? d.far_cur ^ 1u : d.far_cur;
+}
+__device__ __forceinline__ uint32_t *dst_FAR(const SolveArgs &a, const PhaseDesc &d) {
+    return far_list_index(d) ? a.FAR1 : a.FAR0;
+}
+__device__ __forceinline__ uint32_t *ctr_FAR(const SolveArgs &a, const PhaseDesc &d) {
+    return &a.ctl->nFar[far_list_index(d)];
 }
 
-__device__ __forceinline__ void stage_pushes(PushCtx &q, WarpStage &ws, const Push &p, uint32_t v) {
+// Stage one (vertex, degree, begin) per pushing lane; flush 32 when full.
+template <int LIST>
+__device__ __forceinline__ void stage_seg(const SolveArgs &a, const PhaseDesc &d, bool pred, uint32_t v,
+                                          uint32_t deg, uint32_t beg, uint32_t *bv, uint32_t *bd, uint32_t *bb,
+                                          uint32_t &cnt) {
+    const uint32_t mask = __ballot_sync(FULL, pred);
+    if (mask == 0u) return;
+    const uint32_t lane = lane_id();
+    if (pred) {
+        const uint32_t k = cnt + __popc(mask & lanemask_lt());
+        bv[k] = v; bd[k] = deg; bb[k] = beg;
+    }
+    cnt += __popc(mask);
+    __syncwarp();
+    if (cnt >= 32u) {
+        if (LIST == 0) flush_seg(bv, bd, bb, 32u, dst_F(a, d), ctr_F(a, d));
+        else flush_seg(bv, bd, bb, 32u, dst_S(a, d), ctr_S(a, d));
+        const uint32_t rest = cnt - 32u;
+        uint32_t x = 0, y = 0, z = 0;
+        if (lane < rest) { x = bv[32 + lane]; y = bd[32 + lane]; z = bb[32 + lane]; }
+        __syncwarp();
+        if (lane < rest) { bv[lane] = x; bd[lane] = y; bb[lane] = z; }
+        __syncwarp();
+        cnt = rest;
+    }
+}
+
+__device__ __forceinline__ void stage_far(const SolveArgs &a, const PhaseDesc &d, bool pred, uint32_t v,
+                                          uint32_t *bv, uint32_t &cnt) {
+    const uint32_t mask = __ballot_sync(FULL, pred);
+    if (mask == 0u) return;
+    const uint32_t lane = lane_id();
+    if (pred) bv[cnt + __popc(mask & lanemask_lt())] = v;
+    cnt += __popc(mask);
+    __syncwarp();
+    if (cnt >= 32u) {
+        flush_ids(bv, 32u, dst_FAR(a, d), ctr_FAR(a, d));
+        const uint32_t rest = cnt - 32u;
+        uint32_t x = 0;
+        if (lane < rest) x = bv[32 + lane];
+        __syncwarp();
+        if (lane < rest) bv[lane] = x;
+        __syncwarp();
+        cnt = rest;
+    }
+}
+
+__device__ __forceinline__ void stage_pushes(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws,
+                                             const Push &p, uint32_t v) {
     if (__ballot_sync(FULL, p.f || p.s || p.far) == 0u) return;
-    stage_seg(p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
-    stage_seg(p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-    stage_id(p.far, v, ws.far, q.nfar, q.FAR, q.nFar);
+    stage_seg<0>(a, d, p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf);
+    stage_seg<1>(a, d, p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns);
+    stage_far(a, d, p.far, v, ws.far, q.nfar);
 }
 
 // Flush the partially filled staging buffers (end of a phase).
-__device__ __forceinline__ void drain_pushes(PushCtx &q, WarpStage &ws) {
-    if (q.nf) flush_seg(ws.fv, ws.fd, ws.fb, q.nf, q.F, q.ctrF);
-    if (q.ns) flush_seg(ws.sv, ws.sd, ws.sb, q.ns, q.S, q.ctrS);
-    if (q.nfar) flush_ids(ws.far, q.nfar, q.FAR, q.nFar);
+__device__ __forceinline__ void drain_pushes(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws) {
+    if (q.nf) flush_seg(ws.fv, ws.fd, ws.fb, q.nf, dst_F(a, d), ctr_F(a, d));
+    if (q.ns) flush_seg(ws.sv, ws.sd, ws.sb, q.ns, dst_S(a, d), ctr_S(a, d));
+    if (q.nfar) flush_ids(ws.far, q.nfar, dst_FAR(a, d), ctr_FAR(a, d));
     __syncwarp();
     q.nf = q.ns = q.nfar = 0u;
 }
@@ -248,10 +252,9 @@ __device__ __forceinline__ void on_improved(const SolveArgs &a, const PhaseDesc 
 
 // LIGHT / HEAVY: relax the arcs of a list, split evenly over the warps.
 template <int DT, bool LIGHT>
-__device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot, WarpStage *stage) {
+__device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot, WarpStage *stage,
+                           uint32_t gw, uint32_t nw_all) {
     const uint32_t lane = lane_id();
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw_all = (gridDim.x * blockDim.x) >> 5;
     const uint4 *list = LIGHT ? (d.cur ? a.F1 : a.F0) : (d.scur ? a.S1 : a.S0);
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[4 * j]
     const uint32_t count = d.count;
@@ -264,7 +267,7 @@ __device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc
     if (gw < nw) {
         const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
         const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
-        PushCtx q = push_ctx(a, d, false);
+        PushCnt q{};
         WarpStage &ws = stage[threadIdx.x >> 5];
         // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
         uint32_t lo = 0, hi = count;
@@ -370,10 +373,10 @@ __device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc
                 const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
                 if (cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k])      // strict distance decrease
                     on_improved<DT>(a, d, arc[k].x, ck[k], p, far_min, improved);
-                stage_pushes(q, ws, p, arc[k].x);
+                stage_pushes(a, d, q, ws, p, arc[k].x);
             }
         }
-        drain_pushes(q, ws);
+        drain_pushes(a, d, q, ws);
         if (lane == 0) {
             if (LIGHT) atomicAdd(&acc.arcs_light, (unsigned long long)(e1 - e0));
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
@@ -387,14 +390,13 @@ __device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc
 // are queued into F and S; the rest stay, and their minimum key bounds the next
 // bucket; stale entries are dropped. Each lane examines kIlp entries at once.
 template <int DT>
-__device__ void phase_select(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, WarpStage *stage) {
+__device__ void phase_select(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, WarpStage *stage,
+                             uint32_t gw, uint32_t nw) {
     const uint32_t lane = lane_id();
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t *in = d.far_cur ? a.FAR1 : a.FAR0;
     const uint32_t count = d.count;
     uint32_t far_min = inf_key<DT>();
-    PushCtx q = push_ctx(a, d, true);
+    PushCnt q{};
     WarpStage &ws = stage[threadIdx.x >> 5];
     const unsigned long long stride = (unsigned long long)nw * 32u * kIlp;
     for (unsigned long long base = (unsigned long long)gw * 32u * kIlp; base < count; base += stride) {
@@ -423,12 +425,12 @@ __device__ void phase_select(const SolveArgs &a, const PhaseDesc &d, BlockAcc &a
             } else if (f[j] == FAR_STALE) {
                 a.far_flag[v[j]] = FAR_NONE;          // stale entry dropped
             }
-            stage_pushes(q, ws, p, v[j]);
+            stage_pushes(a, d, q, ws, p, v[j]);
         }
     }
-    drain_pushes(q, ws);
+    drain_pushes(a, d, q, ws);
     if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
-    if (threadIdx.x == 0 && blockIdx.x == 0) atomicAdd(&acc.far_scanned, (unsigned long long)count);
+    if (gw == 0 && lane == 0) atomicAdd(&acc.far_scanned, (unsigned long long)count);
 }
 
 // ---------------------------------------------------------------------------
@@ -537,6 +539,8 @@ __device__ void serial_step(const SolveArgs &a) {
     if (next_mode == MODE_LIGHT) { nd.count = (uint32_t)(ctrF[s.cur] >> 32); nd.arcs = (uint32_t)ctrF[s.cur]; }
     else if (next_mode == MODE_HEAVY) { nd.count = (uint32_t)(ctrS[s.scur] >> 32); nd.arcs = (uint32_t)ctrS[s.scur]; }
     else if (next_mode == MODE_SELECT) nd.count = nFar[s.far_cur];
+    // little work: one block runs the phase without a grid-wide barrier
+    nd.solo = (next_mode == MODE_SELECT ? nd.count : nd.arcs) <= a.solo_work ? 1u : 0u;
     // write back: consumed counters, serial state, descriptor
     if (resetF) c->ctrF[rF] = 0ull;
     if (resetS) c->ctrS[rS] = 0ull;
@@ -585,8 +589,11 @@ __device__ __forceinline__ void acc_init(BlockAcc &acc) {
 
 // Grid-wide barrier with a serial step, every wait bounded by timeout_ns.
 // Returns false when the solve must stop (done, error recorded, or timed out).
+// With run_serial false (after a solo stretch, whose serial steps block 0
+// already ran) the last arrival only releases; blocks that wait through a solo
+// stretch poll slowly so that they do not load the L2 the solo block uses.
 template <int DT>
-__device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
+__device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool run_serial, bool patient) {
     __syncthreads();
     if (threadIdx.x == 0) {
         Ctl *c = a.ctl;
@@ -594,21 +601,30 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
         __threadfence();
         const unsigned gen = vload(&c->bar_gen);
         const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
+        if (run_serial && arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
         if (arrived == a.nblocks - 1u) {
             atomicExch(&c->bar_count, 0u);
             __threadfence();
-            serial_step<DT>(a);
+            if (run_serial) serial_step<DT>(a);
             __threadfence();
             atomicExch(&c->bar_gen, gen + 1u);
         } else {
-            const uint64_t t0 = globaltimer();
+            // bounded wait: timeout_ns without progress (a solo block's serial
+            // steps advance ss.phases, which restarts the clock)
+            uint64_t t0 = globaltimer();
+            int64_t seen = patient ? vload(&c->ss.phases) : 0;
             while (vload(&c->bar_gen) == gen) {
                 if (vload(&c->err) != 0) break;
-                if ((int64_t)(globaltimer() - t0) > a.timeout_ns) {
+                const uint64_t now = globaltimer();
+                if (patient) {
+                    const int64_t ph = vload(&c->ss.phases);
+                    if (ph != seen) { seen = ph; t0 = now; }
+                }
+                if ((int64_t)(now - t0) > a.timeout_ns) {
                     atomicCAS(&c->err, 0, (int)DSSSP_ERR_TIMEOUT);
                     break;
                 }
+                if (patient) __nanosleep(500);
             }
             __threadfence();
         }
@@ -620,11 +636,11 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok) {
 
 template <int DT>
 __device__ __forceinline__ void run_phase(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot,
-                                          WarpStage *stage) {
+                                          WarpStage *stage, uint32_t gw, uint32_t nw) {
     switch (d.mode) {
-    case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot, stage); break;
-    case MODE_HEAVY: phase_arcs<DT, false>(a, d, acc, slot, stage); break;
-    case MODE_SELECT: phase_select<DT>(a, d, acc, stage); break;
+    case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot, stage, gw, nw); break;
+    case MODE_HEAVY: phase_arcs<DT, false>(a, d, acc, slot, stage, gw, nw); break;
+    case MODE_SELECT: phase_select<DT>(a, d, acc, stage, gw, nw); break;
     default: break;
     }
 }
@@ -638,13 +654,45 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     __shared__ int s_ok;
     if (a.test_hook == DSSSP_HOOK_STALL_BARRIER && blockIdx.x == 1) return;
     if (threadIdx.x == 0) acc_init<DT>(acc);
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
+    bool have_desc = false;
     for (;;) {
-        if (threadIdx.x == 0) read_desc(a.ctl, s_desc);
-        __syncthreads();
-        const PhaseDesc &d = s_desc;
-        if (d.mode == MODE_DONE) break;
-        run_phase<DT>(a, d, acc, slot, stage);
-        if (!grid_barrier<DT>(a, acc, &s_ok)) break;
+        if (!have_desc) {
+            if (threadIdx.x == 0) read_desc(a.ctl, s_desc);
+            __syncthreads();
+        }
+        have_desc = false;
+        if (s_desc.mode == MODE_DONE) break;
+        // A solo phase (little work) runs on block 0 only: its phases follow each
+        // other with block-level synchronisation and the serial step in thread 0,
+        // while the other blocks wait in the grid barrier until a phase with work
+        // for the whole grid (or the end) comes.
+        const bool solo = s_desc.solo != 0u;
+        if (!solo || blockIdx.x == 0) run_phase<DT>(a, s_desc, acc, slot, stage, solo ? wib : gw, solo ? nwb : nw);
+        if (solo && blockIdx.x == 0) {
+            __threadfence();             // list entries and flags reach L2 before the serial step reads them
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                flush_far_min(a.ctl, acc, inf_key<DT>());
+                __threadfence();
+                serial_step<DT>(a);
+                read_desc(a.ctl, s_desc);
+                s_ok = vload(&a.ctl->err) == 0;
+            }
+            __syncthreads();
+            if (!s_ok) break;
+            if (s_desc.solo && s_desc.mode != MODE_DONE) {
+                have_desc = true;        // next solo phase right away
+                continue;
+            }
+            if (!grid_barrier<DT>(a, acc, &s_ok, false, false)) break;   // release the waiting blocks
+        } else if (solo) {
+            if (!grid_barrier<DT>(a, acc, &s_ok, false, true)) break;
+        } else {
+            if (!grid_barrier<DT>(a, acc, &s_ok, true, false)) break;
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) flush_stats(a.ctl, acc);
@@ -664,7 +712,8 @@ __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __syncthreads();
     const PhaseDesc &d = s_desc;
     if (d.mode != MODE) return;
-    run_phase<DT>(a, d, acc, slot, stage);
+    run_phase<DT>(a, d, acc, slot, stage, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                  (gridDim.x * blockDim.x) >> 5);
     __syncthreads();
     if (threadIdx.x == 0) {
         flush_far_min(a.ctl, acc, inf_key<DT>());
@@ -716,6 +765,7 @@ __global__ void k_init(SolveArgs a) {
         d.T = s.T;
         d.count = (uint32_t)(c->ctrF[0] >> 32);
         d.arcs = (uint32_t)c->ctrF[0];
+        d.solo = d.arcs <= a.solo_work ? 1u : 0u;
         c->desc = d;
         a.F0[0] = make_uint4(a.src, 0u, vs.x, 0u);
         a.S0[0] = make_uint4(a.src, 0u, vs.y, 0u);
