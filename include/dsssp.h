@@ -54,7 +54,8 @@ typedef enum {
     DSSSP_ERR_CUDA = 6,          /* a CUDA runtime call failed                                   */
     DSSSP_ERR_NO_TAPE = 7,       /* reserved                                                     */
     DSSSP_ERR_OOM = 8,           /* a device allocation failed                                   */
-    DSSSP_ERR_UNSUPPORTED = 9    /* the device or launch shape cannot run this entry point      */
+    DSSSP_ERR_UNSUPPORTED = 9,   /* the device or launch shape cannot run this entry point      */
+    DSSSP_ERR_TOO_LARGE = 10     /* the graph exceeds dsssp_solve_noalloc's fixed working memory */
 } dsssp_status;
 
 typedef enum { DSSSP_I32 = 0, DSSSP_F32 = 1 } dsssp_dtype;
@@ -170,6 +171,33 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
 /* Wait for the handle's outstanding work on `stream` and return (and clear)
  * the first device-side status recorded by asynchronous solves. */
 dsssp_status dsssp_graph_sync(dsssp_graph *g, void *stream);
+
+/* A solve that allocates no memory at all. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that runs
+ * under an allocator it must not bypass, within a memory budget fixed in
+ * advance, or where a device allocation would synchronise the device or fail.
+ * It returns the same distances and predecessors as dsssp_solve (bit for bit),
+ * reading the caller's CSR directly and keeping all of its working state in one
+ * fixed array compiled into the library (about 11 MB, held by every GPU that
+ * loads the library until the process exits).
+ *   n           number of vertices, 1 <= n <= 131072 (larger graphs:
+ *               DSSSP_ERR_TOO_LARGE); m arcs, m <= 2^31 - 1;
+ *   row_ptr, col, w   DEVICE pointers: int64[n+1], int32[m], int32 or float32[m]
+ *               (dtype); read only, never copied or modified;
+ *   src, delta  as for dsssp_solve;
+ *   dist, pred  DEVICE outputs, n entries each (pred may be NULL), written only
+ *               on success.
+ * The call validates the CSR on the device and waits for the solve.
+ * The first call on a device looks up the device address of the fixed array
+ * (once per device, with that device current); make that first call before
+ * capturing `stream` into a CUDA graph. Every call uses the same array and
+ * clears what it needs first, so calls that overlap on the GPU (for example on
+ * two streams) race: serialise them.
+ * Errors: INVALID_ARG, TOO_LARGE, BAD_GRAPH, NEG_WEIGHT, TIMEOUT, NOT_CONVERGED,
+ * CUDA, UNSUPPORTED. */
+dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
+                                 const void *w, dsssp_dtype dtype, int32_t src, double delta,
+                                 void *dist, int32_t *pred, void *stream);
 
 #ifdef __cplusplus
 }

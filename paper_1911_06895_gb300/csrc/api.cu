@@ -208,6 +208,7 @@ const char *dsssp_status_string(dsssp_status s) {
     case DSSSP_ERR_NO_TAPE: return "no tape";
     case DSSSP_ERR_OOM: return "out of device memory";
     case DSSSP_ERR_UNSUPPORTED: return "unsupported device or launch shape";
+    case DSSSP_ERR_TOO_LARGE: return "graph exceeds the fixed working memory of the no-allocation solve";
     }
     return "unknown status";
 }

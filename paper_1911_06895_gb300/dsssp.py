@@ -34,6 +34,7 @@ DSSSP_ERR_CUDA = 6
 DSSSP_ERR_NO_TAPE = 7
 DSSSP_ERR_OOM = 8
 DSSSP_ERR_UNSUPPORTED = 9
+DSSSP_ERR_TOO_LARGE = 10
 
 DSSSP_I32 = 0
 DSSSP_F32 = 1
@@ -86,9 +87,13 @@ dsssp_solve = _fn("dsssp_solve", ctypes.c_int,
                   [_vp, _i32, ctypes.c_double, _vp, _vp, ctypes.POINTER(dsssp_options),
                    ctypes.POINTER(dsssp_stats), _vp])
 dsssp_graph_sync = _fn("dsssp_graph_sync", ctypes.c_int, [_vp, _vp])
+dsssp_solve_noalloc = _fn("dsssp_solve_noalloc", ctypes.c_int,
+                          [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, _i32, ctypes.c_double, _vp, _vp, _vp])
 
 EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create", "dsssp_graph_destroy",
-            "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync"]
+            "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc"]
+
+NOALLOC_MAX_VERTICES = 1 << 17
 
 
 class DsssError(RuntimeError):
