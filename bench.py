@@ -122,13 +122,34 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
+def sources_for_rank(g, n_sources: int, rank: int) -> list[int]:
+    """Weak scaling: rank r solves its own n_sources sources of the same graph
+    (rank 0 gets the workload's own sources)."""
+    import graphgen
+    return [int(s) for s in graphgen.random_sources(g, n_sources, 2 + 1000 * rank)]
+
+
+def max_over_ranks(x: float, device: str = "cpu") -> float:
+    """Largest value of x over all ranks of the default process group (the
+    slowest rank's time); x itself when no process group is initialised."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_gteps(m: int, solves_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: every rank's arcs x solves over the slowest rank's time."""
+    return m * solves_per_rank * world / seconds / 1e9
+
+
 def build_workload(scale: int, n_sources: int, rank: int):
     import graphgen.workloads as W
     g, _, deltas = W.rmat22_unit(scale=scale, n_sources=n_sources)
-    import graphgen
-    # weak scaling: rank r draws its own sources from the same graph
-    srcs = [int(s) for s in graphgen.random_sources(g, n_sources, 2 + 1000 * rank)]
-    return g, srcs, deltas
+    return g, sources_for_rank(g, n_sources, rank), deltas
 
 
 def cpu_oracle_gteps(g, sources, threads=None):
@@ -256,14 +277,10 @@ def main():
         torch.cuda.synchronize()
         clk = clocks.stop()
         h.sync(stream)
-        elapsed_ms = t0.elapsed_time(t1)
-        if dist_pg:
-            tt = torch.tensor([elapsed_ms], device="cuda")
-            dist_pg.all_reduce(tt, op=dist_pg.ReduceOp.MAX)
-            elapsed_ms = float(tt.item())
+        elapsed_ms = max_over_ranks(t0.elapsed_time(t1), "cuda")
         ms_per_step = elapsed_ms / args.steps
         solves = len(deltas) * len(srcs)
-        gteps = g.m * solves * world / (ms_per_step * 1e-3) / 1e9
+        gteps = job_gteps(g.m, solves, world, ms_per_step * 1e-3)
 
         # per-Delta GTEPS and roofline of the solve (events around each solve call)
         per_delta = {}
@@ -382,12 +399,8 @@ def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args):
     for _ in range(steps):
         step()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t) / steps
-    if dist_pg:
-        tt = torch.tensor([dt], device="cuda")
-        dist_pg.all_reduce(tt, op=dist_pg.ReduceOp.MAX)
-        dt = float(tt.item())
-    return {"value": g.m * solves * world / dt / 1e9, "unit": "GTEPS",
+    dt = max_over_ranks((time.perf_counter() - t) / steps, "cuda")
+    return {"value": job_gteps(g.m, solves, world, dt), "unit": "GTEPS",
             "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes + g.w.nbytes),
             "d2h_bytes_per_step": int(solves * g.n * 8), "ms_per_step": dt * 1e3, "steps": steps}
 
