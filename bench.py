@@ -295,13 +295,13 @@ def main():
             tot_light_ns += sum(st["ns_light"] for st in stats[d])
             per_delta[str(d)].update({
                 "buckets": sum(st["buckets"] for st in stats[d]) / len(srcs),
-                "phases": sum(st["light_phases"] + st["heavy_phases"] + st["select_phases"]
+                "phases": sum(st["light_phases"] + st["heavy_phases"] + st["rebin_phases"]
                               for st in stats[d]) / len(srcs),
                 "arcs_relaxed_per_solve": sum(st["arcs_light"] + st["arcs_heavy"] for st in stats[d]) / len(srcs),
                 "kernel_us_per_solve": sum(st["ns_total"] for st in stats[d]) / len(srcs) / 1e3,
                 "us_light": sum(st["ns_light"] for st in stats[d]) / len(srcs) / 1e3,
                 "us_heavy": sum(st["ns_heavy"] for st in stats[d]) / len(srcs) / 1e3,
-                "us_select": sum(st["ns_select"] for st in stats[d]) / len(srcs) / 1e3,
+                "us_rebin": sum(st["ns_rebin"] for st in stats[d]) / len(srcs) / 1e3,
                 "light_phases": sum(st["light_phases"] for st in stats[d]) / len(srcs),
                 "arcs_light": sum(st["arcs_light"] for st in stats[d]) / len(srcs),
                 "improvements": sum(st["improvements"] for st in stats[d]) / len(srcs),

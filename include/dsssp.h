@@ -86,9 +86,8 @@ typedef struct {
     int32_t  mode;          /* dsssp_mode; default DSSSP_MODE_PERSISTENT                        */
     int32_t  block_size;    /* threads per block, multiple of 32, <= 512; default 512           */
     int32_t  grid_size;     /* blocks of the persistent kernel; default = all co-resident blocks */
-    int32_t  solo_work;     /* phases with at most this many arcs (light/heavy) or far-pile
-                               entries (next-bucket search) run on one block without grid
-                               barriers; default 8192, -1 disables                              */
+    int32_t  solo_work;     /* phases with at most this many arcs or list entries run on one
+                               block without grid barriers; default 2048, -1 disables            */
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
@@ -101,16 +100,16 @@ typedef struct {
     int64_t buckets;          /* non-empty buckets processed                                   */
     int64_t light_phases;     /* light relaxation rounds (inner loop of Fig. 1)                */
     int64_t heavy_phases;     /* heavy passes                                                   */
-    int64_t select_phases;    /* next-bucket searches (far-pile compactions)                   */
+    int64_t rebin_phases;     /* refills of the bucket-slot window from the overflow list       */
     int64_t vertices_light;   /* sum of |frontier| over light rounds                           */
     int64_t vertices_heavy;   /* sum of |S| over heavy passes                                   */
     int64_t arcs_light;       /* light arcs relaxed                                             */
     int64_t arcs_heavy;       /* heavy arcs relaxed                                             */
-    int64_t far_scanned;      /* far-pile entries examined by next-bucket searches             */
+    int64_t far_scanned;      /* overflow entries examined by window refills                    */
     int64_t improvements;     /* strict distance decreases                                      */
     int64_t ns_light;         /* device time in light rounds                                    */
     int64_t ns_heavy;         /* device time in heavy passes                                    */
-    int64_t ns_select;        /* device time in next-bucket searches                           */
+    int64_t ns_rebin;         /* device time in window refills                                  */
     int64_t ns_total;         /* device time of the whole solve kernel                          */
     int64_t ns_first_arrival; /* sum over phases: phase start to the first block's barrier arrival */
     int64_t ns_arrival_spread;/* sum over phases: first to last barrier arrival                  */

@@ -136,14 +136,17 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     size_t bytes = 0;
     const size_t o_packed = bytes; bytes += up(n * 8);
     const size_t o_near = bytes;   bytes += up(n * 4);
-    const size_t o_far = bytes;    bytes += up(n * 4);
     const size_t o_s = bytes;      bytes += up(n * 4);
-    const size_t o_f0 = bytes;     bytes += up(n * 16);
-    const size_t o_f1 = bytes;     bytes += up(n * 16);
-    const size_t o_s0 = bytes;     bytes += up(n * 16);
-    const size_t o_s1 = bytes;     bytes += up(n * 16);
-    const size_t o_far0 = bytes;   bytes += up(n * 4);
-    const size_t o_far1 = bytes;   bytes += up(n * 4);
+    const size_t o_b = bytes;      bytes += up(n * 4);
+    const size_t o_ovf = bytes;    bytes += up(n * 4);
+    const size_t o_f0 = bytes;     bytes += up(n * 8);
+    const size_t o_f1 = bytes;     bytes += up(n * 8);
+    const size_t o_s0 = bytes;     bytes += up(n * 8);
+    const size_t o_s1 = bytes;     bytes += up(n * 8);
+    const size_t o_sl = bytes;     bytes += up(n * 8 * kSlots);
+    const size_t o_sh = bytes;     bytes += up(n * 4 * kSlots);
+    const size_t o_ov0 = bytes;    bytes += up(n * 4);
+    const size_t o_ov1 = bytes;    bytes += up(n * 4);
     const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
     const size_t o_sticky = bytes; bytes += up(sizeof(int32_t));
     char *base = nullptr;
@@ -155,14 +158,17 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     SolveArgs &a = g->args;
     a.packed = (unsigned long long *)(base + o_packed);
     a.near_stamp = (uint32_t *)(base + o_near);
-    a.far_flag = (uint32_t *)(base + o_far);
     a.s_stamp = (uint32_t *)(base + o_s);
-    a.F0 = (uint4 *)(base + o_f0);
-    a.F1 = (uint4 *)(base + o_f1);
-    a.S0 = (uint4 *)(base + o_s0);
-    a.S1 = (uint4 *)(base + o_s1);
-    a.FAR0 = (uint32_t *)(base + o_far0);
-    a.FAR1 = (uint32_t *)(base + o_far1);
+    a.b_stamp = (uint32_t *)(base + o_b);
+    a.ov_flag = (uint32_t *)(base + o_ovf);
+    a.F0 = (uint2 *)(base + o_f0);
+    a.F1 = (uint2 *)(base + o_f1);
+    a.S0 = (uint2 *)(base + o_s0);
+    a.S1 = (uint2 *)(base + o_s1);
+    a.SL = (uint2 *)(base + o_sl);
+    a.SH = (uint32_t *)(base + o_sh);
+    a.OV0 = (uint32_t *)(base + o_ov0);
+    a.OV1 = (uint32_t *)(base + o_ov1);
     a.ctl = (Ctl *)(base + o_ctl);
     g->ctl = a.ctl;
     g->sticky = (int32_t *)(base + o_sticky);
@@ -175,7 +181,7 @@ void fill_stats(const Ctl &ctl, int grid, int block, dsssp_stats *s) {
     s->buckets = st[ST_BUCKETS];
     s->light_phases = st[ST_LIGHT];
     s->heavy_phases = st[ST_HEAVY];
-    s->select_phases = st[ST_SELECT];
+    s->rebin_phases = st[ST_REBIN];
     s->vertices_light = st[ST_VLIGHT];
     s->vertices_heavy = st[ST_VHEAVY];
     s->arcs_light = st[ST_ALIGHT];
@@ -184,7 +190,7 @@ void fill_stats(const Ctl &ctl, int grid, int block, dsssp_stats *s) {
     s->improvements = st[ST_IMPROVE];
     s->ns_light = st[ST_NSLIGHT];
     s->ns_heavy = st[ST_NSHEAVY];
-    s->ns_select = st[ST_NSSELECT];
+    s->ns_rebin = st[ST_NSREBIN];
     s->ns_total = st[ST_NSTOTAL];
     s->ns_first_arrival = st[ST_NSFIRST];
     s->ns_arrival_spread = st[ST_NSSPREAD];
@@ -222,7 +228,7 @@ dsssp_status dsssp_options_default(dsssp_options *opt) {
     opt->grid_size = 0;
     opt->max_phases = (int64_t)1 << 26;
     opt->timeout_ns = 2000000000LL;
-    opt->solo_work = 8192;
+    opt->solo_work = 2048;
     return DSSSP_OK;
 }
 

@@ -97,46 +97,61 @@ __host__ __device__ inline uint32_t light_max_key(int dtype, double delta) {
 // ----------------------------------------------------------------------------
 // Solver phases. Each phase is one grid-wide step separated by a barrier.
 enum Mode : uint32_t {
-    MODE_LIGHT = 0,    // relax light arcs of the frontier F  (t_Req = A_L^T (t o t_Bi))
-    MODE_HEAVY = 1,    // relax heavy arcs of S               (t_Req = A_H^T (t o S))
-    MODE_SELECT = 2,   // next non-empty bucket: compact the far pile into F and S
+    MODE_LIGHT = 0,    // relax light arcs of the frontier  (t_Req = A_L^T (t o t_Bi))
+    MODE_HEAVY = 1,    // relax heavy arcs of S             (t_Req = A_H^T (t o S))
+    MODE_REBIN = 2,    // move overflow vertices into the bucket slots of a new window
     MODE_DONE = 3
 };
 
-// Work lists F (light segments) and S (heavy segments) hold uint4 entries
-// (vertex, exclusive arc offset of the entry within its list, segment begin, 0).
-// An entry is appended with one 64-bit atomicAdd of (1 << 32 | segment length)
-// on the list's counter, so entry positions and arc offsets are consistent and
-// a phase can split the list's flattened arcs evenly over all warps.
+// Buckets. Section III-B's B_j are kept explicitly for a window of kSlots
+// consecutive buckets [wbase, wbase + kSlots): when a vertex's distance drops
+// into bucket j of the window (j > i, the current bucket), it is appended once
+// to slot j - wbase -- to the slot's arc list when it has light arcs, to its
+// heavy-only list otherwise. A later decrease into a lower bucket leaves the
+// entry stale; stale entries are recognised by their key (below the slot's
+// lower edge) and skipped. Distances beyond the window go to the overflow list,
+// which is redistributed into a new window when the current one is used up.
+constexpr uint32_t kSlots = 32;
+
+// Arc lists (frontier F, set S, slot lists) hold uint2 entries (vertex, exclusive
+// arc offset of the entry within its list). An entry is appended with one
+// 64-bit atomicAdd of (entries << 32 | arcs) per 32 staged entries, so entry
+// positions and arc offsets agree and a phase splits the list's flattened arcs
+// evenly over all warps. A vertex's arc segment comes from vinfo.
 //
 // Control block. The serial step of a barrier (one thread) loads SerialState
 // and the list counters in one batch, decides the next phase in registers and
-// publishes a PhaseDesc that every block reads with four 16-byte loads, so a
-// phase change costs a few memory round trips instead of one per field.
+// publishes a PhaseDesc that every block reads with four 16-byte loads.
 
 // Everything a block needs to run a phase (64 bytes).
 struct alignas(64) PhaseDesc {
     uint32_t mode;
-    uint32_t cur;           // F list being read (0/1); F pushes go to cur^1
-    uint32_t scur;          // S list being read by a heavy pass
+    uint32_t cur;           // F list read (0/1) when not reading a slot; F pushes go to cur^1
+    uint32_t scur;          // S list read by a heavy pass
     uint32_t spush;         // S list receiving pushes in this phase
     uint32_t sstamp;        // S stamp of those pushes
-    uint32_t far_cur;       // far list being read (SELECT) or appended to
     uint32_t qstamp;        // stamp of pushes into the next frontier
-    uint32_t T;             // key < T  <=>  bucket <= i
-    uint32_t count;         // entries of the list this phase reads
-    uint32_t arcs;          // arcs of that list (LIGHT / HEAVY)
+    uint32_t T;             // key < T  <=>  bucket <= i (the current bucket)
+    uint32_t T_lo;          // entries of a slot list with key < T_lo are stale (0: none)
+    uint32_t slot;          // LIGHT: slot read by the first round of a bucket, kSlots otherwise
+    uint32_t count;         // entries of the arc list this phase reads (REBIN: overflow entries)
+    uint32_t arcs;          // arcs of that list
+    uint32_t count2;        // first round: heavy-only entries of the slot
+    uint32_t ov_cur;        // overflow list read by REBIN / appended to otherwise
     uint32_t solo;          // 1: block 0 alone runs this phase (little work), the others wait
-    uint32_t pad[5];
+    uint32_t wbase32;       // first bucket of the slot window (low 32 bits, for slot stamps)
+    uint32_t pad;
 };
 
 // State only the serial step reads and writes.
 struct alignas(16) SerialState {
-    uint32_t mode, cur, scur, far_cur, qstamp, sround, T, pad0;
-    int64_t bucket;
+    uint32_t mode, cur, scur, ov_cur, qstamp, sround, T, T_lo;
+    int64_t bucket;         // current bucket i
+    int64_t wbase;          // first bucket of the slot window
     int64_t phases;
     uint64_t t_last;        // %globaltimer at the previous barrier
     uint64_t t_start;
+    uint64_t pad0;
     long long st[16];
 };
 
@@ -145,23 +160,28 @@ struct Ctl {
     unsigned int bar_count;
     unsigned int bar_gen;
     int32_t err;            // first dsssp_status != OK
-    uint32_t pad0[29];
-    PhaseDesc desc;
-    // counters updated with atomics during a phase: (entries << 32) | arcs
-    unsigned long long ctrF[2];
-    unsigned long long ctrS[2];
-    uint32_t nFar[2];
-    uint32_t far_min;       // lower bound on the keys of live far-pile entries
-    uint32_t pad1;
+    uint32_t pad0;
     uint64_t t_first;       // %globaltimer of the first arrival at the current barrier
-    uint32_t pad2[6];
+    uint32_t pad1[26];
+    PhaseDesc desc;
+    // key thresholds of the window: bucket wbase + t starts at key thr[t]
+    uint32_t thr[kSlots + 1];
+    uint32_t pad2[15];
+    // counters updated with atomics during a phase
+    unsigned long long ctrF[2];          // (entries << 32) | arcs
+    unsigned long long ctrS[2];
+    unsigned long long ctrSL[kSlots];    // slot arc lists
+    uint32_t nSH[kSlots];                // slot heavy-only lists
+    uint32_t nOV[2];                     // overflow lists
+    uint32_t ov_min;                     // lower bound on the keys of live overflow entries
+    uint32_t pad3[13];
     SerialState ss;
 };
 
 enum StatIdx {
-    ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_SELECT = 3, ST_VLIGHT = 4, ST_VHEAVY = 5,
+    ST_BUCKETS = 0, ST_LIGHT = 1, ST_HEAVY = 2, ST_REBIN = 3, ST_VLIGHT = 4, ST_VHEAVY = 5,
     ST_ALIGHT = 6, ST_AHEAVY = 7, ST_FARSCAN = 8, ST_IMPROVE = 9, ST_NSLIGHT = 10, ST_NSHEAVY = 11,
-    ST_NSSELECT = 12, ST_NSTOTAL = 13, ST_NSFIRST = 14, ST_NSSPREAD = 15
+    ST_NSREBIN = 12, ST_NSTOTAL = 13, ST_NSFIRST = 14, ST_NSSPREAD = 15
 };
 
 // Per-vertex arc segments of the split layout: [x, y) light, [y, z) heavy.
@@ -171,12 +191,15 @@ struct SolveArgs {
     const uint4 *vinfo;             // n
     const uint2 *arcs;              // m: (head, weight bits), light-first per row
     unsigned long long *packed;     // n
-    uint32_t *near_stamp;           // n
-    uint32_t *far_flag;             // n: 0 no entry, 1 live entry, 2 stale entry
-    uint32_t *s_stamp;              // n
-    uint4 *F0, *F1;                 // n each
-    uint4 *S0, *S1;                 // n each
-    uint32_t *FAR0, *FAR1;          // n each
+    uint32_t *near_stamp;           // n: phase stamp of the last push into the next frontier
+    uint32_t *s_stamp;              // n: bucket stamp of the last push into S
+    uint32_t *b_stamp;              // n: (bucket + 1) of the last push into a slot
+    uint32_t *ov_flag;              // n: 1 while the vertex has a live overflow entry
+    uint2 *F0, *F1;                 // n each
+    uint2 *S0, *S1;                 // n each
+    uint2 *SL;                      // kSlots x n
+    uint32_t *SH;                   // kSlots x n
+    uint32_t *OV0, *OV1;            // n each
     Ctl *ctl;
     double delta;
     int64_t timeout_ns;
@@ -185,7 +208,7 @@ struct SolveArgs {
     uint32_t m;
     uint32_t src;
     uint32_t inf_key;
-    uint32_t solo_work;             // phases with at most this many arcs / far entries run solo
+    uint32_t solo_work;             // phases with at most this much work run solo
     int32_t dtype;
     int32_t test_hook;
     uint32_t nblocks;

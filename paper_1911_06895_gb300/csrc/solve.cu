@@ -1,22 +1,23 @@
 // solve.cu -- the delta-stepping hot path on the GPU (Fig. 1; Sections III-IV).
 //
 // One solve is a sequence of grid-wide phases:
-//   LIGHT   relax the light arcs of the frontier F (the vertices of bucket i
-//           whose distances have not been relaxed yet): t_Req = A_L^T (t o t_Bi),
+//   LIGHT   relax the light arcs of the frontier (the vertices of bucket i whose
+//           distances have not been relaxed yet): t_Req = A_L^T (t o t_Bi),
 //           fused with the re-introduction filter (t_Req < t) o t_Bi and with
 //           t = min(t, t_Req) (Section IV-C; the fusion of Section VI-B) through
-//           one 64-bit atomicMin per arc on packed[v] = key(t[v]) << 32 | pred[v];
+//           one 64-bit atomicMin per arc on packed[v] = key(t[v]) << 32 | pred[v].
+//           The first round of a bucket reads the bucket's own slot list (B_i of
+//           Section III-B, kept explicitly) and also puts its vertices into S.
 //   HEAVY   relax the heavy arcs of S, the vertices processed in bucket i:
 //           t_Req = A_H^T (t o S) (Section III-D, Fig. 1);
-//   SELECT  the next non-empty bucket: i = bucket(min key of the far pile),
-//           then the far pile is compacted into F and S (Fig. 1's outer loop;
+//   REBIN   when the window of bucket slots is used up, the overflow list is
+//           distributed into the slots of the next window (Fig. 1's outer loop;
 //           empty buckets are skipped).
 // A vertex whose distance strictly decreases into bucket <= i is queued once
-// per phase: its light segment goes to the next F and, once per bucket, its
-// heavy segment to S (S = S u t_Bi, Fig. 1). A decrease into a later bucket
-// puts it on the far pile.
+// per phase into the next frontier and, once per bucket, into S; a decrease
+// into a later bucket of the window appends it once to that bucket's slot.
 //
-// Load balance: F and S entries carry their arc offset within the list, so a
+// Load balance: arc lists carry each entry's arc offset within the list, so a
 // phase splits the list's flattened arcs into equal contiguous slices, one per
 // warp (merge-path). Each warp finds its first entry with a 32-ary search and
 // walks a 32-entry window of the list; each 32-arc step maps arcs to owners
@@ -25,8 +26,9 @@
 //
 // DSSSP_MODE_PERSISTENT runs all phases in one cooperative launch; every
 // barrier wait is bounded by timeout_ns and ends the kernel with
-// DSSSP_ERR_TIMEOUT instead of hanging. DSSSP_MODE_STEPPED launches one kernel
-// per phase and runs the serial step as a 1-thread kernel.
+// DSSSP_ERR_TIMEOUT instead of hanging. Phases with little work run on block 0
+// alone (solo). DSSSP_MODE_STEPPED launches one kernel per phase and runs the
+// serial step as a 1-thread kernel.
 #include "dsssp_internal.cuh"
 
 namespace dsssp {
@@ -37,8 +39,7 @@ constexpr uint32_t FULL = 0xffffffffu;
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 constexpr int kIlp = 4;                // independent 32-arc steps per warp iteration
 constexpr uint32_t kMinSlice = 32u * kIlp;
-
-enum FarFlag : uint32_t { FAR_NONE = 0, FAR_LIVE = 1, FAR_STALE = 2 };
+constexpr uint32_t kNoSlot = kSlots;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -74,21 +75,29 @@ __device__ __forceinline__ constexpr uint32_t inf_key() {
     return DT == DSSSP_F32 ? KEY_INF_F32 : KEY_INF_I32;
 }
 
-// ---------------------------------------------------------------------------
-// Per-warp staging of pushes in shared memory: a list counter is touched once
-// per 32 staged entries, not once per 32-arc step, and list stores are 32-wide.
-struct WarpStage {
-    uint32_t fv[64], fd[64], fb[64];     // next-frontier entries (vertex, light degree, begin)
-    uint32_t sv[64], sd[64], sb[64];     // S entries (vertex, heavy degree, begin)
-    uint32_t far[64];                    // far-pile entries
+// Per-block copy of what a phase needs: the descriptor and the window's key
+// thresholds (bucket wbase + t starts at key thr[t]).
+struct BlockView {
+    PhaseDesc d;
+    uint32_t thr[kSlots + 1];
 };
 
-// Write n <= 32 staged segment entries (lanes < n) to an F or S list.
-__device__ __forceinline__ void flush_seg(const uint32_t *bv, const uint32_t *bd, const uint32_t *bb, uint32_t n,
-                                          uint4 *list, unsigned long long *ctr) {
+// ---------------------------------------------------------------------------
+// Per-warp staging of pushes in shared memory: a list counter is touched once
+// per 32 staged entries, not once per 32-arc step, and list stores are wide.
+struct WarpStage {
+    uint32_t fv[64], fd[64];             // next frontier (vertex, light degree)
+    uint32_t sv[64], sd[64];             // S (vertex, heavy degree)
+    uint32_t bt[64], bv[64], bd[64];     // bucket slots (slot, vertex, light degree; 0: heavy-only list)
+    uint32_t ov[64];                     // overflow
+};
+
+// Append n <= 32 staged (vertex, degree) entries (lanes < n) to an arc list.
+__device__ __forceinline__ void flush_arc_entries(const uint32_t *bv, const uint32_t *bd, uint32_t n, uint2 *list,
+                                                  unsigned long long *ctr) {
     const uint32_t lane = lane_id();
     const bool has = lane < n;
-    const uint32_t v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u, b = has ? bb[lane] : 0u;
+    const uint32_t v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u;
     uint32_t incl = d;
     #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -99,7 +108,7 @@ __device__ __forceinline__ void flush_seg(const uint32_t *bv, const uint32_t *bd
     unsigned long long old = 0;
     if (lane == 0) old = atomicAdd(ctr, ((unsigned long long)n << 32) | tot);
     old = __shfl_sync(FULL, old, 0);
-    if (has) list[(uint32_t)(old >> 32) + lane] = make_uint4(v, (uint32_t)old + incl - d, b, 0u);
+    if (has) list[(uint32_t)(old >> 32) + lane] = make_uint2(v, (uint32_t)old + incl - d);
 }
 
 __device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32_t *list, uint32_t *counter) {
@@ -110,74 +119,126 @@ __device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32
     if (lane < n) list[base + lane] = bv[lane];
 }
 
+// Append n <= 32 staged slot entries: lanes are grouped by (slot, list) and
+// each group takes one atomic on its slot's counter.
+__device__ __forceinline__ void flush_slot_entries(const SolveArgs &a, const uint32_t *bt, const uint32_t *bv,
+                                                   const uint32_t *bd, uint32_t n) {
+    const uint32_t lane = lane_id();
+    const bool has = lane < n;
+    const uint32_t t = has ? bt[lane] : 0u, v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u;
+    const uint32_t key = (t << 1) | (d == 0u ? 1u : 0u);
+    uint32_t todo = __ballot_sync(FULL, has);
+    Ctl *c = a.ctl;
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const uint32_t lkey = __shfl_sync(FULL, key, leader);
+        const uint32_t grp = __ballot_sync(FULL, has && key == lkey);
+        todo &= ~grp;
+        const bool mine = (grp >> lane) & 1u;
+        const uint32_t slot = lkey >> 1;
+        const uint32_t rank = __popc(grp & lanemask_lt());
+        if (lkey & 1u) {                                   // heavy-only list of the slot
+            uint32_t base = 0;
+            if ((int)lane == leader) base = atomicAdd(&c->nSH[slot], (uint32_t)__popc(grp));
+            base = __shfl_sync(FULL, base, leader);
+            if (mine) a.SH[(size_t)slot * a.n + base + rank] = v;
+        } else {                                           // arc list of the slot
+            const uint32_t dd = mine ? d : 0u;
+            uint32_t incl = dd;
+            #pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t x = __shfl_up_sync(FULL, incl, o);
+                if ((int)lane >= o) incl += x;
+            }
+            const uint32_t tot = __shfl_sync(FULL, incl, 31);
+            unsigned long long old = 0;
+            if ((int)lane == leader) old = atomicAdd(&c->ctrSL[slot], ((unsigned long long)__popc(grp) << 32) | tot);
+            old = __shfl_sync(FULL, old, leader);
+            if (mine) a.SL[(size_t)slot * a.n + (uint32_t)(old >> 32) + rank] = make_uint2(v, (uint32_t)old + incl - dd);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Block-local accumulators flushed to the control block.
 struct BlockAcc {
-    uint32_t far_min;
+    uint32_t ov_min;
     unsigned long long arcs_light, arcs_heavy, improvements, far_scanned;
 };
 
 // Pending pushes of one lane in one step.
 struct Push {
-    bool f, s, far;
-    uint32_t fdeg, fbeg, sdeg, sbeg;
+    bool f, s, b, ov;
+    uint32_t fdeg, sdeg, slot, bdeg;
 };
 
-// The warp's staged counts. The destination lists follow from the phase
-// descriptor (in shared memory) and are resolved only when a buffer is flushed,
-// so they do not hold registers in the relaxation loop. LIGHT/HEAVY append to
-// the current far list; SELECT rebuilds the far pile into the other one.
+// The warp's staged counts; destination lists follow from the phase descriptor.
 struct PushCnt {
-    uint32_t nf, ns, nfar;
+    uint32_t nf, ns, nb, nov;
 };
 
-__device__ __forceinline__ uint4 *dst_F(const SolveArgs &a, const PhaseDesc &d) { return d.cur ? a.F0 : a.F1; }
+__device__ __forceinline__ uint2 *dst_F(const SolveArgs &a, const PhaseDesc &d) { return d.cur ? a.F0 : a.F1; }
 __device__ __forceinline__ unsigned long long *ctr_F(const SolveArgs &a, const PhaseDesc &d) {
     return &a.ctl->ctrF[d.cur ^ 1u];
 }
-__device__ __forceinline__ uint4 *dst_S(const SolveArgs &a, const PhaseDesc &d) { return d.spush ? a.S1 : a.S0; }
+__device__ __forceinline__ uint2 *dst_S(const SolveArgs &a, const PhaseDesc &d) { return d.spush ? a.S1 : a.S0; }
 __device__ __forceinline__ unsigned long long *ctr_S(const SolveArgs &a, const PhaseDesc &d) {
     return &a.ctl->ctrS[d.spush];
 }
-__device__ __forceinline__ uint32_t far_list_index(const PhaseDesc &d) {
-    return d.mode == MODE_SELECT ? d.far_cur ^ 1u : d.far_cur;
-}
-__device__ __forceinline__ uint32_t *dst_FAR(const SolveArgs &a, const PhaseDesc &d) {
-    return far_list_index(d) ? a.FAR1 : a.FAR0;
-}
-__device__ __forceinline__ uint32_t *ctr_FAR(const SolveArgs &a, const PhaseDesc &d) {
-    return &a.ctl->nFar[far_list_index(d)];
+// LIGHT/HEAVY append to the current overflow list; REBIN rebuilds it into the other one
+__device__ __forceinline__ uint32_t ov_index(const PhaseDesc &d) {
+    return d.mode == MODE_REBIN ? d.ov_cur ^ 1u : d.ov_cur;
 }
 
-// Stage one (vertex, degree, begin) per pushing lane; flush 32 when full.
-template <int LIST>
-__device__ __forceinline__ void stage_seg(const SolveArgs &a, const PhaseDesc &d, bool pred, uint32_t v,
-                                          uint32_t deg, uint32_t beg, uint32_t *bv, uint32_t *bd, uint32_t *bb,
-                                          uint32_t &cnt) {
+// Stage one entry per pushing lane of `kind`; flush 32 when the buffer is full.
+__device__ __forceinline__ void stage_arc_entry(bool pred, uint32_t v, uint32_t deg, uint32_t *bv, uint32_t *bd,
+                                                uint32_t &cnt, uint2 *list, unsigned long long *ctr) {
     const uint32_t mask = __ballot_sync(FULL, pred);
     if (mask == 0u) return;
     const uint32_t lane = lane_id();
     if (pred) {
         const uint32_t k = cnt + __popc(mask & lanemask_lt());
-        bv[k] = v; bd[k] = deg; bb[k] = beg;
+        bv[k] = v; bd[k] = deg;
     }
     cnt += __popc(mask);
     __syncwarp();
     if (cnt >= 32u) {
-        if (LIST == 0) flush_seg(bv, bd, bb, 32u, dst_F(a, d), ctr_F(a, d));
-        else flush_seg(bv, bd, bb, 32u, dst_S(a, d), ctr_S(a, d));
+        flush_arc_entries(bv, bd, 32u, list, ctr);
         const uint32_t rest = cnt - 32u;
-        uint32_t x = 0, y = 0, z = 0;
-        if (lane < rest) { x = bv[32 + lane]; y = bd[32 + lane]; z = bb[32 + lane]; }
+        uint32_t x = 0, y = 0;
+        if (lane < rest) { x = bv[32 + lane]; y = bd[32 + lane]; }
         __syncwarp();
-        if (lane < rest) { bv[lane] = x; bd[lane] = y; bb[lane] = z; }
+        if (lane < rest) { bv[lane] = x; bd[lane] = y; }
         __syncwarp();
         cnt = rest;
     }
 }
 
-__device__ __forceinline__ void stage_far(const SolveArgs &a, const PhaseDesc &d, bool pred, uint32_t v,
-                                          uint32_t *bv, uint32_t &cnt) {
+__device__ __forceinline__ void stage_slot_entry(const SolveArgs &a, bool pred, uint32_t slot, uint32_t v,
+                                                 uint32_t deg, WarpStage &ws, uint32_t &cnt) {
+    const uint32_t mask = __ballot_sync(FULL, pred);
+    if (mask == 0u) return;
+    const uint32_t lane = lane_id();
+    if (pred) {
+        const uint32_t k = cnt + __popc(mask & lanemask_lt());
+        ws.bt[k] = slot; ws.bv[k] = v; ws.bd[k] = deg;
+    }
+    cnt += __popc(mask);
+    __syncwarp();
+    if (cnt >= 32u) {
+        flush_slot_entries(a, ws.bt, ws.bv, ws.bd, 32u);
+        const uint32_t rest = cnt - 32u;
+        uint32_t x = 0, y = 0, z = 0;
+        if (lane < rest) { x = ws.bt[32 + lane]; y = ws.bv[32 + lane]; z = ws.bd[32 + lane]; }
+        __syncwarp();
+        if (lane < rest) { ws.bt[lane] = x; ws.bv[lane] = y; ws.bd[lane] = z; }
+        __syncwarp();
+        cnt = rest;
+    }
+}
+
+__device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, uint32_t &cnt, uint32_t *list,
+                                         uint32_t *counter) {
     const uint32_t mask = __ballot_sync(FULL, pred);
     if (mask == 0u) return;
     const uint32_t lane = lane_id();
@@ -185,7 +246,7 @@ __device__ __forceinline__ void stage_far(const SolveArgs &a, const PhaseDesc &d
     cnt += __popc(mask);
     __syncwarp();
     if (cnt >= 32u) {
-        flush_ids(bv, 32u, dst_FAR(a, d), ctr_FAR(a, d));
+        flush_ids(bv, 32u, list, counter);
         const uint32_t rest = cnt - 32u;
         uint32_t x = 0;
         if (lane < rest) x = bv[32 + lane];
@@ -198,106 +259,171 @@ __device__ __forceinline__ void stage_far(const SolveArgs &a, const PhaseDesc &d
 
 __device__ __forceinline__ void stage_pushes(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws,
                                              const Push &p, uint32_t v) {
-    if (__ballot_sync(FULL, p.f || p.s || p.far) == 0u) return;
-    stage_seg<0>(a, d, p.f, v, p.fdeg, p.fbeg, ws.fv, ws.fd, ws.fb, q.nf);
-    stage_seg<1>(a, d, p.s, v, p.sdeg, p.sbeg, ws.sv, ws.sd, ws.sb, q.ns);
-    stage_far(a, d, p.far, v, ws.far, q.nfar);
+    if (__ballot_sync(FULL, p.f || p.s || p.b || p.ov) == 0u) return;
+    stage_arc_entry(p.f, v, p.fdeg, ws.fv, ws.fd, q.nf, dst_F(a, d), ctr_F(a, d));
+    stage_arc_entry(p.s, v, p.sdeg, ws.sv, ws.sd, q.ns, dst_S(a, d), ctr_S(a, d));
+    stage_slot_entry(a, p.b, p.slot, v, p.bdeg, ws, q.nb);
+    const uint32_t oi = ov_index(d);
+    stage_id(p.ov, v, ws.ov, q.nov, oi ? a.OV1 : a.OV0, &a.ctl->nOV[oi]);
 }
 
 // Flush the partially filled staging buffers (end of a phase).
 __device__ __forceinline__ void drain_pushes(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws) {
-    if (q.nf) flush_seg(ws.fv, ws.fd, ws.fb, q.nf, dst_F(a, d), ctr_F(a, d));
-    if (q.ns) flush_seg(ws.sv, ws.sd, ws.sb, q.ns, dst_S(a, d), ctr_S(a, d));
-    if (q.nfar) flush_ids(ws.far, q.nfar, dst_FAR(a, d), ctr_FAR(a, d));
+    if (q.nf) flush_arc_entries(ws.fv, ws.fd, q.nf, dst_F(a, d), ctr_F(a, d));
+    if (q.ns) flush_arc_entries(ws.sv, ws.sd, q.ns, dst_S(a, d), ctr_S(a, d));
+    if (q.nb) flush_slot_entries(a, ws.bt, ws.bv, ws.bd, q.nb);
+    if (q.nov) {
+        const uint32_t oi = ov_index(d);
+        flush_ids(ws.ov, q.nov, oi ? a.OV1 : a.OV0, &a.ctl->nOV[oi]);
+    }
     __syncwarp();
-    q.nf = q.ns = q.nfar = 0u;
+    q.nf = q.ns = q.nb = q.nov = 0u;
 }
 
+// ---------------------------------------------------------------------------
 // Queue v for bucket i (its key is now below T): once per phase into the next
-// F (its light segment), once per bucket into S (its heavy segment). A live
-// far-pile entry of v becomes stale. The loads are issued together with the
-// stamp exchange; they are simply unused when v is already queued.
-__device__ __forceinline__ void queue_near(const SolveArgs &a, const PhaseDesc &d, uint32_t v, Push &p,
-                                           bool mark_far) {
+// frontier (its light segment), once per bucket into S (its heavy segment).
+// The loads are issued together with the stamp exchange.
+__device__ __forceinline__ void queue_near(const SolveArgs &a, const PhaseDesc &d, uint32_t v, Push &p) {
     const uint32_t prev = atomicExch(a.near_stamp + v, d.qstamp);
     const uint4 vi = a.vinfo[v];
     const uint32_t ss = __ldcg(a.s_stamp + v);
-    const uint32_t ff = mark_far ? __ldcg(a.far_flag + v) : FAR_NONE;
     if (prev == d.qstamp) return;
     p.fdeg = vi.y - vi.x;
-    p.fbeg = vi.x;
     p.f = p.fdeg != 0u;
     if (ss != d.sstamp) {
         a.s_stamp[v] = d.sstamp;
         p.sdeg = vi.z - vi.y;
-        p.sbeg = vi.y;
         p.s = p.sdeg != 0u;
     }
-    if (ff == FAR_LIVE) a.far_flag[v] = FAR_STALE;
+}
+
+// Slot of key k in the window: the largest t with thr[t] <= k (thr[0] <= k < thr[kSlots]).
+__device__ __forceinline__ uint32_t slot_of(const uint32_t *thr, uint32_t k) {
+    uint32_t lo = 0, hi = kSlots;          // thr[lo] <= k < thr[hi]
+    #pragma unroll
+    for (int it = 0; it < 5; ++it) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (thr[mid] <= k) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// A later bucket: append v once to its slot (if the window holds it) or to the
+// overflow list.
+template <int DT>
+__device__ __forceinline__ void queue_later(const SolveArgs &a, const BlockView &bvw, uint32_t v, uint32_t ckey,
+                                            Push &p, uint32_t &ov_min) {
+    if (ckey < bvw.thr[kSlots]) {
+        const uint32_t t = slot_of(bvw.thr, ckey);
+        const uint32_t stamp = bvw.d.wbase32 + t + 1u;    // bucket + 1: one entry per (vertex, bucket)
+        const uint32_t prev = atomicExch(a.b_stamp + v, stamp);
+        const uint4 vi = a.vinfo[v];
+        if (prev != stamp) {
+            p.b = true;
+            p.slot = t;
+            p.bdeg = vi.y - vi.x;
+        }
+    } else {
+        ov_min = min(ov_min, ckey);
+        p.ov = atomicExch(a.ov_flag + v, 1u) == 0u;
+    }
 }
 
 // relax(v, new_dist) of Section III-C, after the packed atomicMin found a strict
-// decrease of t[v]: v re-enters bucket i ((t_Req < t) o t_Bi) or goes to the far pile.
+// decrease of t[v]: back into bucket i ((t_Req < t) o t_Bi) or into a later bucket.
 template <int DT>
-__device__ __forceinline__ void on_improved(const SolveArgs &a, const PhaseDesc &d, uint32_t v, uint32_t ckey,
-                                            Push &p, uint32_t &far_min, uint32_t &improved) {
+__device__ __forceinline__ void on_improved(const SolveArgs &a, const BlockView &bvw, uint32_t v, uint32_t ckey,
+                                            Push &p, uint32_t &ov_min, uint32_t &improved) {
     ++improved;
-    if (ckey < d.T) {
-        queue_near(a, d, v, p, true);
-    } else {
-        far_min = min(far_min, ckey);
-        p.far = atomicExch(a.far_flag + v, FAR_LIVE) == FAR_NONE;
+    if (ckey < bvw.d.T) queue_near(a, bvw.d, v, p);
+    else queue_later<DT>(a, bvw, v, ckey, p, ov_min);
+}
+
+// First round of a bucket: every vertex of the bucket's slot (both lists) that
+// is still in the bucket joins S (S = S u B_i).
+__device__ void slot_entries_into_S(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws, uint32_t gw,
+                                    uint32_t nw) {
+    const uint32_t lane = lane_id();
+    const uint2 *sl = a.SL + (size_t)d.slot * a.n;
+    const uint32_t *sh = a.SH + (size_t)d.slot * a.n;
+    const uint32_t total = d.count + d.count2;
+    for (uint32_t base = gw * 32u; base < total; base += nw * 32u) {
+        const uint32_t idx = base + lane;
+        Push p{};
+        uint32_t v = 0;
+        if (idx < total) {
+            v = idx < d.count ? __ldcs(sl + idx).x : __ldcs(sh + (idx - d.count));
+            if (v < a.n) {
+                const uint32_t k = (uint32_t)(__ldcg(a.packed + v) >> 32);
+                const uint4 vi = a.vinfo[v];
+                if (k >= d.T_lo && __ldcg(a.s_stamp + v) != d.sstamp) {
+                    a.s_stamp[v] = d.sstamp;
+                    p.sdeg = vi.z - vi.y;
+                    p.s = p.sdeg != 0u;
+                }
+            }
+        }
+        stage_pushes(a, d, q, ws, p, v);
     }
 }
 
 // LIGHT / HEAVY: relax the arcs of a list, split evenly over the warps.
 template <int DT, bool LIGHT>
-__device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot, WarpStage *stage,
+__device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &acc, int *slot, WarpStage *stage,
                            uint32_t gw, uint32_t nw_all) {
+    const PhaseDesc &d = bvw.d;
     const uint32_t lane = lane_id();
-    const uint4 *list = LIGHT ? (d.cur ? a.F1 : a.F0) : (d.scur ? a.S1 : a.S0);
-    const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[4 * j]
+    const bool from_slot = LIGHT && d.slot < kNoSlot;
+    const uint2 *list = LIGHT ? (from_slot ? a.SL + (size_t)d.slot * a.n : (d.cur ? a.F1 : a.F0))
+                              : (d.scur ? a.S1 : a.S0);
+    const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[2 * j]
     const uint32_t count = d.count;
     const uint32_t E = d.arcs;
+    const uint32_t T_lo = d.T_lo;
+    uint32_t ov_min = inf_key<DT>();
+    uint32_t improved = 0;
+    PushCnt q{};
+    WarpStage &ws = stage[threadIdx.x >> 5];
+    if (from_slot) slot_entries_into_S(a, d, q, ws, gw, nw_all);
     // at least kMinSlice arcs per warp: small phases use few warps
     const uint32_t want_w = (E + kMinSlice - 1u) / kMinSlice;
     const uint32_t nw = want_w < nw_all ? want_w : nw_all;
-    uint32_t far_min = inf_key<DT>();
-    uint32_t improved = 0;
     if (gw < nw) {
         const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
         const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
-        PushCnt q{};
-        WarpStage &ws = stage[threadIdx.x >> 5];
         // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
         uint32_t lo = 0, hi = count;
         while (hi - lo > 32u) {
             const uint32_t step = (hi - lo + 31u) >> 5;
             const uint32_t p = lo + lane * step;
-            const bool ok = p < hi && __ldcg(offs + 4ull * p) <= e0;
+            const bool ok = p < hi && __ldcg(offs + 2ull * p) <= e0;
             const uint32_t k = 31u - __clz(__ballot_sync(FULL, ok));
             lo += k * step;
             hi = min(hi, lo + step);
         }
         {
             const uint32_t p = lo + lane;
-            const bool ok = p < hi && __ldcg(offs + 4ull * p) <= e0;
+            const bool ok = p < hi && __ldcg(offs + 2ull * p) <= e0;
             lo += 31u - __clz(__ballot_sync(FULL, ok));
         }
-        // window: lane k holds entry jw + k; wend = arc offset just past the window
+        // window: lane k holds entry jw + k; wend = arc offset just past the window.
+        // A stale slot entry (its vertex moved to a lower bucket) gets key INF and is skipped.
         uint32_t jw = lo, wv = 0, woff = 0xFFFFFFFFu, wbeg = 0, wkey = inf_key<DT>(), wend = 0;
         auto load_window = [&](uint32_t j) {
             const uint32_t idx = j + lane;
             if (idx < count) {
-                const uint4 en = __ldcs(list + idx);
+                const uint2 en = __ldcs(list + idx);
                 wv = en.x < a.n ? en.x : 0u;          // defensive: ids come from device lists
                 woff = en.y;
-                wbeg = en.z;
-                wkey = (uint32_t)(__ldcg(a.packed + wv) >> 32);
+                const uint32_t k = (uint32_t)(__ldcg(a.packed + wv) >> 32);
+                const uint4 vi = a.vinfo[wv];
+                wbeg = LIGHT ? vi.x : vi.y;
+                wkey = k >= T_lo ? k : inf_key<DT>();
             } else {
                 wv = 0; woff = 0xFFFFFFFFu; wbeg = 0; wkey = inf_key<DT>();
             }
-            wend = (j + 32u < count) ? __ldcg(offs + 4ull * (j + 32u)) : E;
+            wend = (j + 32u < count) ? __ldcg(offs + 2ull * (j + 32u)) : E;
         };
         load_window(jw);
         int *sl = slot + (threadIdx.x >> 5) * 32;
@@ -346,7 +472,8 @@ __device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc
                     okey[k] = __shfl_sync(FULL, wkey, own);
                     const uint32_t e = base + lane;
                     ai[k] = obeg + (e - ooff);
-                    ok[k] = e < e1 && ai[k] < a.m;     // defensive bound; true when lists are consistent
+                    // defensive bound (true when lists are consistent); stale owners are skipped
+                    ok[k] = e < e1 && ai[k] < a.m && okey[k] < inf_key<DT>();
                 }
             }
             uint2 arc[kIlp];
@@ -372,64 +499,52 @@ __device__ void phase_arcs(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc
                 Push p{};
                 const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
                 if (cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k])      // strict distance decrease
-                    on_improved<DT>(a, d, arc[k].x, ck[k], p, far_min, improved);
+                    on_improved<DT>(a, bvw, arc[k].x, ck[k], p, ov_min, improved);
                 stage_pushes(a, d, q, ws, p, arc[k].x);
             }
         }
-        drain_pushes(a, d, q, ws);
         if (lane == 0) {
             if (LIGHT) atomicAdd(&acc.arcs_light, (unsigned long long)(e1 - e0));
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
         }
     }
-    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
+    drain_pushes(a, d, q, ws);
+    if (ov_min < inf_key<DT>()) atomicMin(&acc.ov_min, ov_min);
     if (improved) atomicAdd(&acc.improvements, (unsigned long long)improved);
 }
 
-// SELECT: compact the far pile. Live entries whose key is below T (bucket <= i)
-// are queued into F and S; the rest stay, and their minimum key bounds the next
-// bucket; stale entries are dropped. Each lane examines kIlp entries at once.
+// REBIN: the window is used up; every live overflow vertex either is stale (its
+// bucket was processed), goes to its slot in the new window, or stays.
 template <int DT>
-__device__ void phase_select(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, WarpStage *stage,
-                             uint32_t gw, uint32_t nw) {
+__device__ void phase_rebin(const SolveArgs &a, const BlockView &bvw, BlockAcc &acc, WarpStage *stage,
+                            uint32_t gw, uint32_t nw) {
+    const PhaseDesc &d = bvw.d;
     const uint32_t lane = lane_id();
-    const uint32_t *in = d.far_cur ? a.FAR1 : a.FAR0;
+    const uint32_t *in = d.ov_cur ? a.OV1 : a.OV0;
     const uint32_t count = d.count;
-    uint32_t far_min = inf_key<DT>();
+    uint32_t ov_min = inf_key<DT>();
     PushCnt q{};
     WarpStage &ws = stage[threadIdx.x >> 5];
-    const unsigned long long stride = (unsigned long long)nw * 32u * kIlp;
-    for (unsigned long long base = (unsigned long long)gw * 32u * kIlp; base < count; base += stride) {
-        uint32_t v[kIlp], f[kIlp], k[kIlp];
-        #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            const unsigned long long idx = base + 32u * j + lane;
-            v[j] = idx < count ? __ldcs(in + idx) : 0xFFFFFFFFu;
-        }
-        #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            f[j] = v[j] < a.n ? __ldcg(a.far_flag + v[j]) : FAR_NONE;
-            k[j] = v[j] < a.n ? (uint32_t)(__ldcg(a.packed + v[j]) >> 32) : inf_key<DT>();
-        }
-        #pragma unroll
-        for (int j = 0; j < kIlp; ++j) {
-            Push p{};
-            if (f[j] == FAR_LIVE) {
-                if (k[j] < d.T) {
-                    a.far_flag[v[j]] = FAR_NONE;
-                    queue_near(a, d, v[j], p, false);
-                } else {
-                    p.far = true;                      // stays on the (rebuilt) far pile
-                    far_min = min(far_min, k[j]);
-                }
-            } else if (f[j] == FAR_STALE) {
-                a.far_flag[v[j]] = FAR_NONE;          // stale entry dropped
+    for (uint32_t base = gw * 32u; base < count; base += nw * 32u) {
+        const uint32_t idx = base + lane;
+        Push p{};
+        uint32_t v = 0xFFFFFFFFu;
+        if (idx < count && (v = __ldcs(in + idx)) < a.n && __ldcg(a.ov_flag + v) == 1u) {
+            const uint32_t k = (uint32_t)(__ldcg(a.packed + v) >> 32);
+            if (k < bvw.thr[0]) {
+                a.ov_flag[v] = 0u;                      // its bucket was processed: stale
+            } else if (k < bvw.thr[kSlots]) {
+                a.ov_flag[v] = 0u;
+                queue_later<DT>(a, bvw, v, k, p, ov_min);
+            } else {
+                p.ov = true;                            // stays for a later window
+                ov_min = min(ov_min, k);
             }
-            stage_pushes(a, d, q, ws, p, v[j]);
         }
+        stage_pushes(a, d, q, ws, p, v);
     }
     drain_pushes(a, d, q, ws);
-    if (far_min < inf_key<DT>()) atomicMin(&acc.far_min, far_min);
+    if (ov_min < inf_key<DT>()) atomicMin(&acc.ov_min, ov_min);
     if (gw == 0 && lane == 0) atomicAdd(&acc.far_scanned, (unsigned long long)count);
 }
 
@@ -439,7 +554,7 @@ __device__ void phase_select(const SolveArgs &a, const PhaseDesc &d, BlockAcc &a
 // phase (the control flow of Fig. 1) in registers, resets consumed counters
 // and publishes the next PhaseDesc.
 template <int DT>
-__device__ void serial_step(const SolveArgs &a) {
+__device__ __noinline__ void serial_step(const SolveArgs &a) {
     Ctl *c = a.ctl;
     SerialState s;
     {
@@ -448,10 +563,14 @@ __device__ void serial_step(const SolveArgs &a) {
         #pragma unroll
         for (int k = 0; k < (int)(sizeof(SerialState) / 16); ++k) dst[k] = __ldcg(src + k);
     }
-    const unsigned long long cf0 = __ldcg(&c->ctrF[0]), cf1 = __ldcg(&c->ctrF[1]);
-    const unsigned long long cs0 = __ldcg(&c->ctrS[0]), cs1 = __ldcg(&c->ctrS[1]);
-    const uint32_t nfar0 = __ldcg(&c->nFar[0]), nfar1 = __ldcg(&c->nFar[1]);
-    const uint32_t far_min = __ldcg(&c->far_min);
+    PhaseDesc od;                                  // the phase that just ended
+    #pragma unroll
+    for (int k = 0; k < 4; ++k)
+        reinterpret_cast<uint4 *>(&od)[k] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + k);
+    unsigned long long ctrF[2] = {__ldcg(&c->ctrF[0]), __ldcg(&c->ctrF[1])};
+    unsigned long long ctrS[2] = {__ldcg(&c->ctrS[0]), __ldcg(&c->ctrS[1])};
+    const uint32_t nov[2] = {__ldcg(&c->nOV[0]), __ldcg(&c->nOV[1])};
+    const uint32_t ov_min = __ldcg(&c->ov_min);
     const uint64_t t_first = __ldcg(&c->t_first);
     const uint64_t now = globaltimer();
     const uint64_t dt = now - s.t_last;
@@ -460,16 +579,13 @@ __device__ void serial_step(const SolveArgs &a) {
         s.st[ST_NSSPREAD] += (long long)(now - t_first);
     }
     s.t_last = now;
-    unsigned long long ctrF[2] = {cf0, cf1}, ctrS[2] = {cs0, cs1};
-    uint32_t nFar[2] = {nfar0, nfar1};
-    bool resetF = false, resetS = false, resetFar = false;   // consumed list counters
-    uint32_t rF = 0, rS = 0, rFar = 0;
     const uint32_t mode = s.mode;
-    PhaseDesc nd{};
     if (mode == MODE_LIGHT) s.st[ST_NSLIGHT] += (long long)dt;
     else if (mode == MODE_HEAVY) s.st[ST_NSHEAVY] += (long long)dt;
-    else if (mode == MODE_SELECT) s.st[ST_NSSELECT] += (long long)dt;
+    else if (mode == MODE_REBIN) s.st[ST_NSREBIN] += (long long)dt;
     s.phases += 1;
+    PhaseDesc nd{};
+    nd.slot = kNoSlot;
     bool done = false;
     if (s.phases >= a.max_phases) {
         atomicCAS(&c->err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
@@ -478,20 +594,28 @@ __device__ void serial_step(const SolveArgs &a) {
         switch (mode) {
         case MODE_LIGHT:
             s.st[ST_LIGHT] += 1;
-            s.st[ST_VLIGHT] += (long long)(ctrF[s.cur] >> 32);
-            resetF = true; rF = s.cur; ctrF[s.cur] = 0ull;
+            if (od.slot < kNoSlot) {               // the bucket's slot is consumed
+                s.st[ST_VLIGHT] += (long long)od.count;
+                c->ctrSL[od.slot] = 0ull;
+                c->nSH[od.slot] = 0u;
+            } else {
+                s.st[ST_VLIGHT] += (long long)(ctrF[s.cur] >> 32);
+                c->ctrF[s.cur] = 0ull;
+                ctrF[s.cur] = 0ull;
+            }
             break;
         case MODE_HEAVY:
             s.st[ST_HEAVY] += 1;
             s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
-            resetS = true; rS = s.scur; ctrS[s.scur] = 0ull;
+            c->ctrS[s.scur] = 0ull;
+            ctrS[s.scur] = 0ull;
             s.scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
             s.sround += 1u;
             break;
-        case MODE_SELECT:
-            s.st[ST_SELECT] += 1;
-            resetFar = true; rFar = s.far_cur; nFar[s.far_cur] = 0u;
-            s.far_cur ^= 1u;
+        case MODE_REBIN:
+            s.st[ST_REBIN] += 1;
+            c->nOV[s.ov_cur] = 0u;
+            s.ov_cur ^= 1u;
             break;
         default:
             done = true;
@@ -499,30 +623,71 @@ __device__ void serial_step(const SolveArgs &a) {
         }
     }
     uint32_t next_mode = MODE_DONE;
-    bool reset_min = false;
     if (!done) {
         s.qstamp += 1u;                            // every phase queues under a fresh stamp
         const uint32_t nxt = s.cur ^ 1u;
         if ((ctrF[nxt] >> 32) != 0ull) {           // inner loop of Fig. 1: while t_Bi != 0
-            if (mode == MODE_SELECT) s.st[ST_BUCKETS] += 1;
             s.cur = nxt;
             next_mode = MODE_LIGHT;
+            nd.count = (uint32_t)(ctrF[nxt] >> 32);
+            nd.arcs = (uint32_t)ctrF[nxt];
         } else if ((ctrS[s.scur] >> 32) != 0ull) { // bucket settled: heavy pass over S
-            if (mode == MODE_SELECT) s.st[ST_BUCKETS] += 1;
             next_mode = MODE_HEAVY;
-        } else if (far_min >= inf_key<DT>() && nFar[s.far_cur] == 0u) {
-            next_mode = MODE_DONE;                 // nothing left in any bucket
-        } else {                                   // next non-empty bucket
-            if (far_min >= inf_key<DT>()) {
-                s.T = 0u;                          // only stale entries remain: drop them
-            } else {
-                const int64_t i = bucket_of_key(far_min, DT, a.delta);
-                s.bucket = i;
-                s.T = i < INT64_MAX ? bucket_floor_key(i + 1, DT, a.delta) : 0u;
-                if (s.T <= far_min) s.T = far_min + 1u;     // always take the smallest live key
+            nd.count = (uint32_t)(ctrS[s.scur] >> 32);
+            nd.arcs = (uint32_t)ctrS[s.scur];
+        } else {
+            // next non-empty bucket of the window: slot counters read 8 at a time
+            const int first = (int)(s.bucket - s.wbase + 1);   // slots before it are consumed
+            int found = -1;
+            unsigned long long fsl = 0ull;
+            uint32_t fsh = 0u;
+            for (int t0 = first < 0 ? 0 : first; t0 < (int)kSlots && found < 0; t0 += 8) {
+                unsigned long long sl[8];
+                uint32_t sh[8];
+                #pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int t = t0 + k < (int)kSlots ? t0 + k : (int)kSlots - 1;
+                    sl[k] = __ldcg(&c->ctrSL[t]);
+                    sh[k] = __ldcg(&c->nSH[t]);
+                }
+                #pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    if (found < 0 && t0 + k < (int)kSlots && ((sl[k] >> 32) != 0ull || sh[k] != 0u)) {
+                        found = t0 + k;
+                        fsl = sl[k];
+                        fsh = sh[k];
+                    }
             }
-            reset_min = true;
-            next_mode = MODE_SELECT;
+            if (found >= 0) {
+                s.bucket = s.wbase + found;
+                s.st[ST_BUCKETS] += 1;
+                s.T_lo = __ldcg(&c->thr[found]);
+                s.T = __ldcg(&c->thr[found + 1]);
+                next_mode = MODE_LIGHT;
+                nd.slot = (uint32_t)found;
+                nd.count = (uint32_t)(fsl >> 32);
+                nd.arcs = (uint32_t)fsl;
+                nd.count2 = fsh;
+            } else if (nov[s.ov_cur] != 0u) {
+                // window used up: the next one starts at the smallest overflow key
+                #pragma unroll
+                for (int t = 0; t < (int)kSlots; ++t) { c->ctrSL[t] = 0ull; c->nSH[t] = 0u; }
+                if (ov_min < inf_key<DT>()) {
+                    const int64_t w = bucket_of_key(ov_min, DT, a.delta);
+                    s.wbase = w;
+                    s.bucket = w - 1;
+                    for (int t = 0; t <= (int)kSlots; ++t) {
+                        uint32_t th = w + t < INT64_MAX ? bucket_floor_key(w + t, DT, a.delta) : inf_key<DT>();
+                        if (t == 1 && th <= ov_min) th = ov_min + 1u;   // the smallest key lands in slot 0
+                        c->thr[t] = th;
+                    }
+                } else {                           // only stale entries remain: drop them all
+                    for (int t = 0; t <= (int)kSlots; ++t) c->thr[t] = inf_key<DT>();
+                }
+                c->ov_min = inf_key<DT>();
+                next_mode = MODE_REBIN;
+                nd.count = nov[s.ov_cur];
+            }
         }
     }
     if (next_mode == MODE_DONE) s.st[ST_NSTOTAL] = (long long)(now - s.t_start);
@@ -533,19 +698,14 @@ __device__ void serial_step(const SolveArgs &a) {
     // S pushes: into the current S, except during a heavy pass, which feeds the next one
     nd.spush = next_mode == MODE_HEAVY ? s.scur ^ 1u : s.scur;
     nd.sstamp = next_mode == MODE_HEAVY ? s.sround + 1u : s.sround;
-    nd.far_cur = s.far_cur;
     nd.qstamp = s.qstamp;
     nd.T = s.T;
-    if (next_mode == MODE_LIGHT) { nd.count = (uint32_t)(ctrF[s.cur] >> 32); nd.arcs = (uint32_t)ctrF[s.cur]; }
-    else if (next_mode == MODE_HEAVY) { nd.count = (uint32_t)(ctrS[s.scur] >> 32); nd.arcs = (uint32_t)ctrS[s.scur]; }
-    else if (next_mode == MODE_SELECT) nd.count = nFar[s.far_cur];
+    nd.T_lo = nd.slot < kNoSlot ? s.T_lo : 0u;
+    nd.ov_cur = s.ov_cur;
+    nd.wbase32 = (uint32_t)s.wbase;
     // little work: one block runs the phase without a grid-wide barrier
-    nd.solo = (next_mode == MODE_SELECT ? nd.count : nd.arcs) <= a.solo_work ? 1u : 0u;
-    // write back: consumed counters, serial state, descriptor
-    if (resetF) c->ctrF[rF] = 0ull;
-    if (resetS) c->ctrS[rS] = 0ull;
-    if (resetFar) c->nFar[rFar] = 0u;
-    if (reset_min) c->far_min = inf_key<DT>();
+    const uint32_t work = next_mode == MODE_REBIN ? nd.count : max(nd.arcs, nd.count + nd.count2);
+    nd.solo = work <= a.solo_work ? 1u : 0u;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&s);
         uint4 *dst = reinterpret_cast<uint4 *>(&c->ss);
@@ -558,17 +718,18 @@ __device__ void serial_step(const SolveArgs &a) {
     }
 }
 
-__device__ __forceinline__ void read_desc(const Ctl *c, PhaseDesc &d) {
-    const uint4 *src = reinterpret_cast<const uint4 *>(&c->desc);
-    uint4 *dst = reinterpret_cast<uint4 *>(&d);
-    #pragma unroll
-    for (int k = 0; k < 4; ++k) dst[k] = __ldcg(src + k);
+// Every thread of the block calls it; fills the block's view of the phase.
+__device__ __forceinline__ void read_view(const Ctl *c, BlockView &v) {
+    for (uint32_t i = threadIdx.x; i < 4u + kSlots + 1u; i += blockDim.x) {
+        if (i < 4u) reinterpret_cast<uint4 *>(&v.d)[i] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + i);
+        else v.thr[i - 4u] = __ldcg(&c->thr[i - 4u]);
+    }
 }
 
-__device__ __forceinline__ void flush_far_min(Ctl *c, BlockAcc &acc, uint32_t inf) {
-    if (acc.far_min < inf) {
-        atomicMin(&c->far_min, acc.far_min);
-        acc.far_min = inf;
+__device__ __forceinline__ void flush_ov_min(Ctl *c, BlockAcc &acc, uint32_t inf) {
+    if (acc.ov_min < inf) {
+        atomicMin(&c->ov_min, acc.ov_min);
+        acc.ov_min = inf;
     }
 }
 
@@ -583,12 +744,11 @@ __device__ __forceinline__ void flush_stats(Ctl *c, BlockAcc &acc) {
 
 template <int DT>
 __device__ __forceinline__ void acc_init(BlockAcc &acc) {
-    acc.far_min = inf_key<DT>();
+    acc.ov_min = inf_key<DT>();
     acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
 }
 
 // Grid-wide barrier with a serial step, every wait bounded by timeout_ns.
-// Returns false when the solve must stop (done, error recorded, or timed out).
 // With run_serial false (after a solo stretch, whose serial steps block 0
 // already ran) the last arrival only releases; blocks that wait through a solo
 // stretch poll slowly so that they do not load the L2 the solo block uses.
@@ -597,7 +757,7 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool 
     __syncthreads();
     if (threadIdx.x == 0) {
         Ctl *c = a.ctl;
-        flush_far_min(c, acc, inf_key<DT>());
+        flush_ov_min(c, acc, inf_key<DT>());
         __threadfence();
         const unsigned gen = vload(&c->bar_gen);
         const unsigned arrived = atomicAdd(&c->bar_count, 1u);
@@ -635,12 +795,12 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool 
 }
 
 template <int DT>
-__device__ __forceinline__ void run_phase(const SolveArgs &a, const PhaseDesc &d, BlockAcc &acc, int *slot,
+__device__ __forceinline__ void run_phase(const SolveArgs &a, const BlockView &v, BlockAcc &acc, int *slot,
                                           WarpStage *stage, uint32_t gw, uint32_t nw) {
-    switch (d.mode) {
-    case MODE_LIGHT: phase_arcs<DT, true>(a, d, acc, slot, stage, gw, nw); break;
-    case MODE_HEAVY: phase_arcs<DT, false>(a, d, acc, slot, stage, gw, nw); break;
-    case MODE_SELECT: phase_select<DT>(a, d, acc, stage, gw, nw); break;
+    switch (v.d.mode) {
+    case MODE_LIGHT: phase_arcs<DT, true>(a, v, acc, slot, stage, gw, nw); break;
+    case MODE_HEAVY: phase_arcs<DT, false>(a, v, acc, slot, stage, gw, nw); break;
+    case MODE_REBIN: phase_rebin<DT>(a, v, acc, stage, gw, nw); break;
     default: break;
     }
 }
@@ -649,7 +809,7 @@ template <int DT>
 __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
     __shared__ WarpStage stage[kMaxWarps];
-    __shared__ PhaseDesc s_desc;
+    __shared__ BlockView view;
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
     if (a.test_hook == DSSSP_HOOK_STALL_BARRIER && blockIdx.x == 1) return;
@@ -657,34 +817,36 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-    bool have_desc = false;
+    bool have_view = false;
     for (;;) {
-        if (!have_desc) {
-            if (threadIdx.x == 0) read_desc(a.ctl, s_desc);
+        if (!have_view) {
+            read_view(a.ctl, view);
             __syncthreads();
         }
-        have_desc = false;
-        if (s_desc.mode == MODE_DONE) break;
+        have_view = false;
+        if (view.d.mode == MODE_DONE) break;
         // A solo phase (little work) runs on block 0 only: its phases follow each
         // other with block-level synchronisation and the serial step in thread 0,
         // while the other blocks wait in the grid barrier until a phase with work
         // for the whole grid (or the end) comes.
-        const bool solo = s_desc.solo != 0u;
-        if (!solo || blockIdx.x == 0) run_phase<DT>(a, s_desc, acc, slot, stage, solo ? wib : gw, solo ? nwb : nw);
+        const bool solo = view.d.solo != 0u;
+        if (!solo || blockIdx.x == 0) run_phase<DT>(a, view, acc, slot, stage, solo ? wib : gw, solo ? nwb : nw);
         if (solo && blockIdx.x == 0) {
             __threadfence();             // list entries and flags reach L2 before the serial step reads them
             __syncthreads();
             if (threadIdx.x == 0) {
-                flush_far_min(a.ctl, acc, inf_key<DT>());
+                flush_ov_min(a.ctl, acc, inf_key<DT>());
                 __threadfence();
                 serial_step<DT>(a);
-                read_desc(a.ctl, s_desc);
+                __threadfence();
                 s_ok = vload(&a.ctl->err) == 0;
             }
             __syncthreads();
             if (!s_ok) break;
-            if (s_desc.solo && s_desc.mode != MODE_DONE) {
-                have_desc = true;        // next solo phase right away
+            read_view(a.ctl, view);
+            __syncthreads();
+            if (view.d.solo && view.d.mode != MODE_DONE) {
+                have_view = true;        // next solo phase right away
                 continue;
             }
             if (!grid_barrier<DT>(a, acc, &s_ok, false, false)) break;   // release the waiting blocks
@@ -703,20 +865,17 @@ template <int DT, uint32_t MODE>
 __global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
     __shared__ WarpStage stage[kMaxWarps];
-    __shared__ PhaseDesc s_desc;
+    __shared__ BlockView view;
     __shared__ BlockAcc acc;
-    if (threadIdx.x == 0) {
-        read_desc(a.ctl, s_desc);
-        acc_init<DT>(acc);
-    }
+    read_view(a.ctl, view);
+    if (threadIdx.x == 0) acc_init<DT>(acc);
     __syncthreads();
-    const PhaseDesc &d = s_desc;
-    if (d.mode != MODE) return;
-    run_phase<DT>(a, d, acc, slot, stage, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+    if (view.d.mode != MODE) return;
+    run_phase<DT>(a, view, acc, slot, stage, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                   (gridDim.x * blockDim.x) >> 5);
     __syncthreads();
     if (threadIdx.x == 0) {
-        flush_far_min(a.ctl, acc, inf_key<DT>());
+        flush_ov_min(a.ctl, acc, inf_key<DT>());
         flush_stats(a.ctl, acc);
     }
 }
@@ -735,8 +894,9 @@ __global__ void k_init(SolveArgs a) {
         // t = inf, t[s] = 0 (Fig. 1); the predecessor of s is s
         a.packed[v] = v == a.src ? (unsigned long long)a.src : unreached;
         a.near_stamp[v] = v == a.src ? 1u : 0u;
-        a.far_flag[v] = FAR_NONE;
         a.s_stamp[v] = v == a.src ? 1u : 0u;
+        a.b_stamp[v] = 0u;
+        a.ov_flag[v] = 0u;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctl *c = a.ctl;
@@ -744,22 +904,28 @@ __global__ void k_init(SolveArgs a) {
         c->bar_count = 0u;
         c->bar_gen = 0u;
         c->err = 0;
+        c->t_first = 0ull;
         SerialState s{};
         s.mode = MODE_LIGHT;      // B_0 = {s}
         s.qstamp = 1u;
         s.sround = 1u;
-        s.T = bucket_floor_key(1, DT, a.delta);
+        s.bucket = 0;
+        s.wbase = 0;
         s.st[ST_BUCKETS] = 1;
         s.t_start = s.t_last = globaltimer();
+        for (int t = 0; t <= (int)kSlots; ++t) c->thr[t] = bucket_floor_key(t, DT, a.delta);
+        s.T = c->thr[1];
         c->ss = s;
         c->ctrF[0] = (vs.y > vs.x) ? ((1ull << 32) | (vs.y - vs.x)) : 0ull;
         c->ctrF[1] = 0ull;
         c->ctrS[0] = (vs.z > vs.y) ? ((1ull << 32) | (vs.z - vs.y)) : 0ull;
         c->ctrS[1] = 0ull;
-        c->nFar[0] = c->nFar[1] = 0u;
-        c->far_min = inf_key<DT>();
+        for (int t = 0; t < (int)kSlots; ++t) { c->ctrSL[t] = 0ull; c->nSH[t] = 0u; }
+        c->nOV[0] = c->nOV[1] = 0u;
+        c->ov_min = inf_key<DT>();
         PhaseDesc d{};
         d.mode = MODE_LIGHT;
+        d.slot = kNoSlot;
         d.qstamp = 1u;
         d.sstamp = 1u;
         d.T = s.T;
@@ -767,8 +933,8 @@ __global__ void k_init(SolveArgs a) {
         d.arcs = (uint32_t)c->ctrF[0];
         d.solo = d.arcs <= a.solo_work ? 1u : 0u;
         c->desc = d;
-        a.F0[0] = make_uint4(a.src, 0u, vs.x, 0u);
-        a.S0[0] = make_uint4(a.src, 0u, vs.y, 0u);
+        a.F0[0] = make_uint2(a.src, 0u);
+        a.S0[0] = make_uint2(a.src, 0u);
     }
 }
 
@@ -820,7 +986,7 @@ cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, in
     switch (mode) {
         DSSSP_PHASE_CASE(MODE_LIGHT)
         DSSSP_PHASE_CASE(MODE_HEAVY)
-        DSSSP_PHASE_CASE(MODE_SELECT)
+        DSSSP_PHASE_CASE(MODE_REBIN)
     default: break;
     }
 #undef DSSSP_PHASE_CASE

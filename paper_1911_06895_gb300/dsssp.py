@@ -54,9 +54,9 @@ class dsssp_options(ctypes.Structure):
 
 class dsssp_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
-        "buckets", "light_phases", "heavy_phases", "select_phases", "vertices_light",
+        "buckets", "light_phases", "heavy_phases", "rebin_phases", "vertices_light",
         "vertices_heavy", "arcs_light", "arcs_heavy", "far_scanned", "improvements", "ns_light",
-        "ns_heavy", "ns_select", "ns_total", "ns_first_arrival", "ns_arrival_spread", "grid_size",
+        "ns_heavy", "ns_rebin", "ns_total", "ns_first_arrival", "ns_arrival_spread", "grid_size",
         "block_size")] + [("reserved", ctypes.c_int64 * 6)]
 
     def as_dict(self) -> dict:

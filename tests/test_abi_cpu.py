@@ -35,7 +35,7 @@ def test_status_strings_and_defaults():
     assert ds.dsssp_status_string(999) == b"unknown status"
     o = ds.make_options()
     assert o.struct_size == ctypes.sizeof(ds.dsssp_options)
-    assert o.block_size == 512 and o.solo_work == 8192 and o.timeout_ns == 2_000_000_000
+    assert o.block_size == 512 and o.solo_work == 2048 and o.timeout_ns == 2_000_000_000
     assert ds.dsssp_options_default(None) == ds.DSSSP_ERR_INVALID_ARG
 
 
