@@ -37,7 +37,13 @@ namespace {
 
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
-constexpr int kIlp = 4;                // independent 32-arc steps per warp iteration
+#ifndef DSSSP_ILP
+#define DSSSP_ILP 4
+#endif
+#ifndef DSSSP_MIN_BLOCKS
+#define DSSSP_MIN_BLOCKS 2
+#endif
+constexpr int kIlp = DSSSP_ILP;        // independent 32-arc steps per warp iteration
 constexpr uint32_t kMinSlice = 32u * kIlp;
 constexpr uint32_t kNoSlot = kSlots;
 
@@ -806,7 +812,7 @@ __device__ __forceinline__ void run_phase(const SolveArgs &a, const BlockView &v
 }
 
 template <int DT>
-__global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
+__global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
     __shared__ WarpStage stage[kMaxWarps];
     __shared__ BlockView view;
@@ -862,7 +868,7 @@ __global__ void __launch_bounds__(512, 2) k_solve_persistent(SolveArgs a) {
 
 // ---- stepped mode: one launch per phase --------------------------------------
 template <int DT, uint32_t MODE>
-__global__ void __launch_bounds__(512, 2) k_phase(SolveArgs a) {
+__global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_phase(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
     __shared__ WarpStage stage[kMaxWarps];
     __shared__ BlockView view;
