@@ -44,9 +44,26 @@ DELTAS = [0.01, 0.05, 0.1, 0.5]
 # Algorithmic bytes (what the method must move):
 #   per frontier / S vertex: 4 (list id) + 16 (arc segments) + 8 (packed[u])
 #   per arc relaxed:         8 (head, weight) + 8 (packed[v] read-modify-write)
-#   per far-pile entry:      4 (id) + 4 (flag) + 8 (packed) + 4 (rewrite)
+#   per overflow entry re-binned: 4 (id) + 4 (flag) + 8 (packed) + 4 (rewrite)
 #   per vertex, init+unpack: 8 + 12 (packed, stamps) + 8 (packed read) + 8 (dist, pred)
 B_VERTEX, B_ARC, B_FAR, B_INIT_UNPACK = 28, 16, 20, 36
+
+
+# DRAM traffic of k_solve_persistent per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum), mean of
+# one launch at each Delta of the sweep (profiles/k_solve_persistent_rmat22_traffic_by_delta.md). It holds only
+# for the kernel source the counters were taken on; any other source reports null.
+TRAFFIC_BYTES_PER_LAUNCH = 3.167e9
+TRAFFIC_SOURCE_SHA256 = "6a73fb5edcab62f2263cf3c80ba4a0156644eb82cbe1d0b30295b976cdc200de"
+
+
+def measured_traffic(scale: int):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1911_06895_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("solve.cu", "dsssp_internal.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return TRAFFIC_BYTES_PER_LAUNCH if (scale == 22 and h.hexdigest() == TRAFFIC_SOURCE_SHA256) else None
 
 
 def algorithmic_bytes(st: dict, n: int) -> int:
@@ -202,7 +219,8 @@ def main():
     ap.add_argument("--cpu-sources", type=int, default=0, help="CPU baseline sample (0: one per core)")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling driver: run this many solves at --profile-delta and exit (for ncu)")
-    ap.add_argument("--profile-delta", type=float, default=0.1)
+    ap.add_argument("--profile-delta", default="0.1",
+                    help="comma-separated Deltas, or 'all' for every Delta of the sweep")
     args = ap.parse_args()
     if args.profile_solves:
         profile_driver(args)
@@ -334,7 +352,8 @@ def main():
                        "l2": "inputs larger than L2 (arcs %.0f MB per Delta)" % (g.m * 8 / 1e6),
                        "split_ms": split_ms, "per_delta": per_delta, "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": measured_traffic(args.scale),
+                         "algorithmic_bytes_per_launch": tot_bytes / max(1, solves), "peak_kind": peak_kind,
                          "kernel": "k_solve_persistent (with its init/unpack launches)",
                          "light_relax_gbs": light_gbs,
                          "light_relax_frac": (light_gbs / peak) if light_gbs else None},
@@ -354,12 +373,16 @@ def profile_driver(args):
     import torch
     import paper_1911_06895_gb300 as ds
     g, srcs, _ = build_workload(args.scale, max(args.profile_solves, 1), 0)
+    deltas = DELTAS if args.profile_delta == "all" else [float(x) for x in args.profile_delta.split(",")]
     h = ds.Graph(g.row_ptr, g.col, g.w)
-    h.prepare(args.profile_delta)
+    for d in deltas:
+        h.prepare(d)
     opt = ds.make_options(mode=args.mode)
-    for s in srcs[:args.profile_solves]:
-        r = h.solve(s, args.profile_delta, options=opt, stats=True)
-        print(json.dumps({"src": s, "delta": args.profile_delta, **r.stats}), flush=True)
+    for d in deltas:
+        for s in srcs[:args.profile_solves]:
+            r = h.solve(s, d, options=opt, stats=True)
+            print(json.dumps({"src": s, "delta": d, "algorithmic_bytes": algorithmic_bytes(r.stats, g.n),
+                              **r.stats}), flush=True)
     torch.cuda.synchronize()
 
 

@@ -38,7 +38,7 @@ namespace {
 constexpr uint32_t FULL = 0xffffffffu;
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 #ifndef DSSSP_ILP
-#define DSSSP_ILP 4
+#define DSSSP_ILP 2
 #endif
 #ifndef DSSSP_MIN_BLOCKS
 #define DSSSP_MIN_BLOCKS 2
