@@ -10,7 +10,9 @@ no code with it. It wraps ``oracle.c`` (plain C, built with gcc) through ctypes:
 * ``delta_la``      delta-stepping in the linear-algebraic form (Fig. 1, left);
 * ``floyd_warshall_i32``  all-pairs brute force for integer weights;
 * ``check_invariants``    arc inequality / predecessor equality checker;
-* ``bucket_index``  the exact bucket function floor(x / Delta) (Section III-B).
+* ``bucket_index``  the exact bucket function floor(x / Delta) (Section III-B);
+* ``tree_gradient`` dL/dw of L = sum_v c[v] * dist[v] by subtree sums of c over
+  the shortest-path tree (float64), for float32 graphs.
 
 Every function takes a graph as (row_ptr int64[n+1], col int32[m], w int32|float32[m]).
 """
@@ -68,6 +70,8 @@ def _load():
         lib.or_check_invariants.argtypes = [c.c_int64, vp, vp, vp, c.c_int, c.c_int32, vp, vp]
         lib.or_bucket_index.restype = c.c_int64
         lib.or_bucket_index.argtypes = [c.c_double, c.c_double]
+        lib.or_tree_gradient.restype = c.c_int
+        lib.or_tree_gradient.argtypes = [c.c_int64, vp, vp, vp, c.c_int32, c.c_double, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -189,3 +193,41 @@ def dijkstra_many(row_ptr, col, w, sources, threads: int | None = None):
     with ThreadPoolExecutor(max_workers=threads) as ex:
         res = list(ex.map(lambda s: dijkstra(row_ptr, col, w, s), sources))
     return [r[0] for r in res], [r[1] for r in res], threads
+
+
+class CycleError(ValueError):
+    """The predecessor graph has a cycle (zero-weight ties): no gradient."""
+
+
+def tree_gradient(row_ptr, col, w, src, delta, c, dist=None, pred=None, out=None):
+    """dL/dw (float64[m], input arc order) of L = sum over reached v of c[v] * dist[v]
+    for one source; dist/pred from ``dijkstra`` unless given. Adds into ``out``."""
+    lib = _load()
+    row_ptr, col, w, dt = _prep(row_ptr, col, w)
+    if dt != F32:
+        raise TypeError("tree_gradient needs float32 weights")
+    n = row_ptr.shape[0] - 1
+    if dist is None or pred is None:
+        dist, pred = dijkstra(row_ptr, col, w, src)
+    dist = np.ascontiguousarray(dist, dtype=np.float32)
+    pred = np.ascontiguousarray(pred, dtype=np.int32)
+    c = np.ascontiguousarray(c, dtype=np.float32)
+    if c.shape[0] < n:
+        raise ValueError("c needs n entries")
+    g = out if out is not None else np.zeros(col.shape[0], dtype=np.float64)
+    rc = lib.or_tree_gradient(n, _ptr(row_ptr), _ptr(col), _ptr(w), int(src), float(delta), _ptr(dist),
+                              _ptr(pred), _ptr(c), _ptr(g))
+    if rc == 3:
+        raise CycleError("predecessor graph has a cycle")
+    _check(rc, "or_tree_gradient")
+    return g
+
+
+def tree_gradient_many(row_ptr, col, w, sources, delta, cs, threads: int | None = None):
+    """Sum over sources k of tree_gradient(..., sources[k], cs[k]); one source per thread."""
+    threads = max(1, min(threads or os.cpu_count() or 1, len(sources)))
+    row_ptr, col, w, _ = _prep(row_ptr, col, w)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda k: tree_gradient(row_ptr, col, w, sources[k], delta, cs[k]),
+                            range(len(sources))))
+    return np.sum(parts, axis=0) if parts else np.zeros(col.shape[0])

@@ -558,3 +558,86 @@ int64_t or_check_invariants(int64_t n, const int64_t *row_ptr, const int32_t *co
     free(t); free(best);
     return bad;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of L = sum over reached v of c[v] * dist[v] with respect to the  */
+/* weights (float32 graphs; the paper defines no gradient -- this is the     */
+/* derivative of its distances). dist[v] is the (+)-sum of the weights on    */
+/* v's shortest-path tree path from s, so raising the weight of v's tree arc */
+/* by eps raises dist[x] by eps for every x in the subtree below v (as long  */
+/* as the tree stays the same): dL/dw(tree arc of v) = sum of c over that     */
+/* subtree, and 0 for arcs outside the tree.                                  */
+/* The tree arc of v is an arc (pred[v], v) whose sum reaches dist[v]; among  */
+/* parallel arcs that do, the first in pred[v]'s light-then-heavy order       */
+/* (light: w <= Delta, Section III-A), input order within each group.         */
+/* Subtree sums are accumulated in double by an explicit post-order walk.    */
+/* grad (m entries) is ADDED to. Returns 3 when the predecessor graph has a   */
+/* cycle (zero-weight ties), where the gradient is undefined.                 */
+
+enum { OR_ECYCLE = 3 };
+
+int or_tree_gradient(int64_t n, const int64_t *row_ptr, const int32_t *col, const float *w,
+                     int32_t src, double delta, const float *dist, const int32_t *pred,
+                     const float *c, double *grad) {
+    if (n <= 0 || src < 0 || src >= n) return OR_EINVAL;
+    int64_t *tree = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    int64_t *head = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int32_t *kids = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t *stack = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int64_t *next = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    double *sum = (double *)malloc((size_t)n * sizeof(double));
+    if (!tree || !head || !kids || !stack || !next || !sum) {
+        free(tree); free(head); free(kids); free(stack); free(next); free(sum);
+        return OR_ENOMEM;
+    }
+    int rc = OR_OK;
+    int64_t reached = 0;
+    /* tree arc of every reached v != src */
+    for (int64_t v = 0; v < n; ++v) {
+        tree[v] = -1;
+        if (isinf(dist[v])) continue;
+        ++reached;
+        if (v == src) continue;
+        int32_t u = pred[v];
+        if (u < 0 || u >= n) { rc = OR_EINVAL; goto out; }
+        for (int pass = 0; pass < 2 && tree[v] < 0; ++pass) {        /* light, then heavy */
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                if (col[e] != v) continue;
+                int light = (double)w[e] <= delta;
+                if ((pass == 0) != light) continue;
+                if (oplus(OR_F32, (double)dist[u], (double)w[e]) == (double)dist[v]) { tree[v] = e; break; }
+            }
+        }
+        if (tree[v] < 0) { rc = OR_EINVAL; goto out; }                /* pred does not realise dist */
+    }
+    /* children lists (counting sort by parent) */
+    for (int64_t v = 0; v <= n; ++v) head[v] = 0;
+    for (int64_t v = 0; v < n; ++v) if (tree[v] >= 0) head[pred[v] + 1]++;
+    for (int64_t v = 0; v < n; ++v) head[v + 1] += head[v];
+    for (int64_t v = 0; v < n; ++v) next[v] = head[v];
+    for (int64_t v = 0; v < n; ++v) if (tree[v] >= 0) kids[next[pred[v]]++] = (int32_t)v;
+    /* post-order from the source: a vertex is finished after all of its children */
+    {
+        int64_t top = 0, visited = 0;
+        for (int64_t v = 0; v < n; ++v) { next[v] = head[v]; sum[v] = 0.0; }
+        stack[top++] = src;
+        while (top > 0) {
+            int32_t v = stack[top - 1];
+            if (next[v] < head[v + 1]) {
+                stack[top++] = kids[next[v]++];
+            } else {
+                --top;
+                ++visited;
+                sum[v] += (double)c[v];
+                if (v != src) {
+                    sum[pred[v]] += sum[v];
+                    grad[tree[v]] += sum[v];
+                }
+            }
+        }
+        if (visited != reached) rc = OR_ECYCLE;                         /* part of the tree hangs off a cycle */
+    }
+out:
+    free(tree); free(head); free(kids); free(stack); free(next); free(sum);
+    return rc;
+}
