@@ -52,10 +52,11 @@ typedef enum {
     DSSSP_ERR_NOT_CONVERGED = 4, /* the phase cap of dsssp_options.max_phases was reached       */
     DSSSP_ERR_TIMEOUT = 5,       /* a bounded device-side wait ran out (dsssp_options.timeout_ns) */
     DSSSP_ERR_CUDA = 6,          /* a CUDA runtime call failed                                   */
-    DSSSP_ERR_NO_TAPE = 7,       /* reserved                                                     */
+    DSSSP_ERR_NO_TAPE = 7,       /* dsssp_backward on a batch without a recorded tree            */
     DSSSP_ERR_OOM = 8,           /* a device allocation failed                                   */
     DSSSP_ERR_UNSUPPORTED = 9,   /* the device or launch shape cannot run this entry point      */
-    DSSSP_ERR_TOO_LARGE = 10     /* the graph exceeds dsssp_solve_noalloc's fixed working memory */
+    DSSSP_ERR_TOO_LARGE = 10,    /* the graph exceeds dsssp_solve_noalloc's fixed working memory */
+    DSSSP_ERR_DEGENERATE = 11    /* the predecessor graph has a cycle (zero-weight ties): no gradient */
 } dsssp_status;
 
 typedef enum { DSSSP_I32 = 0, DSSSP_F32 = 1 } dsssp_dtype;
@@ -197,6 +198,105 @@ dsssp_status dsssp_graph_sync(dsssp_graph *g, void *stream);
 dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                                  const void *w, dsssp_dtype dtype, int32_t src, double delta,
                                  void *dist, int32_t *pred, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batches: many independent solves in one persistent launch.               */
+/*                                                                          */
+/* Delta-stepping's parallelism within one solve is the work of one bucket   */
+/* phase (Section III-C); independent solves -- many sources on one graph,   */
+/* or many graphs -- add a second, coarser dimension. A batch solves every   */
+/* instance with the same method and the same exact results as dsssp_solve;  */
+/* each instance keeps its own bucket state and is processed start to end by */
+/* one block of a persistent kernel that takes instances from a device-side  */
+/* queue (largest graphs first). A batch is a plan: its instance table,      */
+/* working memory and a CUDA graph of its launch are built once, then run    */
+/* any number of times.                                                     */
+
+typedef struct dsssp_batch dsssp_batch;
+
+/* dsssp_batch_create flags */
+#define DSSSP_BATCH_TAPE 0x1u    /* record every instance's shortest-path tree (parent and the input
+                                    index of its tree arc) for dsssp_backward; float32 graphs only */
+
+/* dsssp_backward flags */
+#define DSSSP_BACKWARD_ACCUMULATE 0x1u  /* add into grad_w instead of overwriting it            */
+
+/* Counters of one instance of the last run (dsssp_batch_sync). */
+typedef struct {
+    int64_t buckets;          /* non-empty buckets processed                                   */
+    int64_t light_phases;     /* light relaxation rounds                                        */
+    int64_t heavy_phases;     /* heavy passes                                                   */
+    int64_t select_phases;    /* next-bucket selections (scans of the instance's far list)      */
+    int64_t arcs_light;       /* light arcs relaxed                                             */
+    int64_t arcs_heavy;       /* heavy arcs relaxed                                             */
+    int64_t improvements;     /* strict distance decreases                                      */
+    int64_t far_scanned;      /* far-list entries examined by selections                        */
+    int64_t ns;               /* device time from the instance's start to its end              */
+    int64_t team;             /* block that solved it                                           */
+    int64_t reserved[6];
+} dsssp_batch_stats;
+
+/* Build a batch (a plan of n_inst solves):
+ *   graphs      HOST array of n_graphs handles, all of one dtype and on the current device;
+ *   delta       HOST array of n_graphs bucket widths (> 0, may be +inf), one per graph;
+ *   n_inst      number of solves, >= 1;
+ *   src         HOST array of n_inst sources (0 <= src < n of its graph);
+ *   src_graph   HOST array of n_inst graph indices, or NULL: every instance on graphs[0];
+ *   dist        HOST array of n_inst DEVICE pointers, each n (of its graph) elements of the
+ *               graph's dtype, written by every run;
+ *   pred        HOST array of n_inst DEVICE pointers (int32[n]) or NULL entries, or NULL;
+ *   flags       DSSSP_BATCH_TAPE or 0;
+ *   opt         NULL, or options (block_size must be 512 or 0; grid_size caps the number of
+ *               blocks; max_phases caps the phases of each instance);
+ *   stream      orders the set-up work (light/heavy splits, tables); the call waits for it;
+ *   out         receives the plan.
+ * The plan keeps the graphs' splits for these Deltas alive (a graph holds at most four) and
+ * the output pointers; graphs must outlive the plan. The caller's arrays are not retained.
+ * Errors: INVALID_ARG, UNSUPPORTED (int32 graphs with DSSSP_BATCH_TAPE, more than four
+ * Deltas held on one graph), OOM, CUDA. */
+dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, const double *delta,
+                                int32_t n_inst, const int32_t *src, const int32_t *src_graph,
+                                void *const *dist, int32_t *const *pred, uint32_t flags,
+                                const dsssp_options *opt, void *stream, dsssp_batch **out);
+
+/* Enqueue one run of every instance on `stream`: a single launch of the plan's CUDA graph
+ * (queue reset + the persistent kernel). Does not wait. Errors: INVALID_ARG, CUDA. */
+dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream);
+
+/* Wait for `stream`, then return (and clear) the first device-side status of the runs and
+ * backward passes since the last sync (NOT_CONVERGED when an instance hit the phase cap,
+ * DEGENERATE from dsssp_backward). stats: NULL or a HOST array of n_inst records, filled
+ * from the last run, in the caller's instance order. */
+dsssp_status dsssp_batch_sync(dsssp_batch *b, dsssp_batch_stats *stats, void *stream);
+
+/* Release a plan (waits for its pending work). */
+dsssp_status dsssp_batch_destroy(dsssp_batch *b);
+
+/* Convenience: create, run once, sync (stats as above, may be NULL), destroy. */
+dsssp_status dsssp_solve_batched(dsssp_graph *const *graphs, int32_t n_graphs, const double *delta,
+                                 int32_t n_inst, const int32_t *src, const int32_t *src_graph,
+                                 void *const *dist, int32_t *const *pred, const dsssp_options *opt,
+                                 dsssp_batch_stats *stats, void *stream);
+
+/* Adjoint of the distances with respect to the weights. The paper has no counterpart: it is
+ * the gradient of L = sum over instances k and reached vertices v of c_k[v] * dist_k[v] for
+ * the distances of the last run of a batch created with DSSSP_BATCH_TAPE. Within the
+ * shortest-path tree of instance k, dist_k[v] is the sum of the weights on the tree path
+ * from the source to v, so dL/dw(u,v) = sum of c_k[x] over the subtree below v when (u,v) is
+ * v's tree arc, and 0 for arcs outside every tree. The tree is taken from the forward run
+ * (pred[v] and the input arc that realised dist[v]; among parallel arcs the one met first in
+ * the light-then-heavy order of u's row); nothing is re-solved. Subtree sums are accumulated
+ * leaves first in float64 and rounded to float32 once.
+ *   c       HOST array of n_inst DEVICE pointers, float32[n] each (entries of unreached
+ *           vertices are ignored);
+ *   grad_w  HOST array of n_graphs DEVICE pointers, float32[m] each, indexed like the
+ *           weights given to dsssp_graph_create;
+ *   flags   DSSSP_BACKWARD_ACCUMULATE or 0.
+ * Ordered on `stream`; does not wait. Errors: INVALID_ARG, NO_TAPE (no tape, or no run yet),
+ * CUDA; DEGENERATE (the predecessor graph of some instance has a cycle) is reported by the
+ * next dsssp_batch_sync. */
+dsssp_status dsssp_backward(dsssp_batch *b, const float *const *c, float *const *grad_w, uint32_t flags,
+                            void *stream);
 
 #ifdef __cplusplus
 }

@@ -10,7 +10,7 @@ not been built (there is no fallback path).
 """
 import importlib
 
-_SUBMODULES = ("build", "dsssp")
+_SUBMODULES = ("build", "dsssp", "autograd")
 
 
 def __getattr__(name):

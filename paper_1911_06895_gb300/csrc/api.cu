@@ -5,79 +5,17 @@
 #include <cstring>
 #include <new>
 
-#include "dsssp_internal.cuh"
+#include "graph.cuh"
 
 using namespace dsssp;
 
-namespace {
-
-constexpr int kSplitCache = 4;
-
-struct Split {
-    double delta = 0.0;
-    bool valid = false;
-    uint64_t last_use = 0;
-    uint2 *arcs = nullptr;      // m
-    uint4 *vinfo = nullptr;     // n
-    uint32_t *perm = nullptr;   // m: split position -> input arc index
-};
-
-struct DeviceGuard {
-    int prev = -1;
-    bool changed = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
-            changed = cudaSetDevice(dev) == cudaSuccess;
-        }
-    }
-    ~DeviceGuard() {
-        if (changed) cudaSetDevice(prev);
-    }
-};
-
-}  // namespace
-
-struct dsssp_graph {
-    int64_t n = 0, m = 0;
-    int dtype = 0;
-    int device = 0;
-    int sm_count = 0;
-    uint32_t *off = nullptr;      // n+1
-    int32_t *col = nullptr;       // m
-    uint32_t *wbits = nullptr;    // m
-    Split splits[kSplitCache];
-    uint64_t use_clock = 0;
-    // solver workspace
-    void *ws = nullptr;
-    size_t ws_bytes = 0;
-    SolveArgs args{};
-    Ctl *ctl = nullptr;           // device
-    Ctl *ctl_host = nullptr;      // pinned host mirror
-    int32_t *sticky = nullptr;    // device: first error of asynchronous solves
-    int occ_block = 0, occ_blocks_per_sm = 0;
-};
-
-namespace {
+namespace dsssp {
 
 dsssp_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DSSSP_OK;
     if (e == cudaErrorMemoryAllocation) return DSSSP_ERR_OOM;
     if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) return DSSSP_ERR_UNSUPPORTED;
     return DSSSP_ERR_CUDA;
-}
-
-#define DSSSP_TRY(expr)                                      \
-    do {                                                     \
-        cudaError_t _e = (expr);                             \
-        if (_e != cudaSuccess) {                             \
-            cudaGetLastError();                              \
-            return cuda_status(_e);                          \
-        }                                                    \
-    } while (0)
-
-__global__ void k_sticky(const Ctl *c, int32_t *sticky) {
-    int e = *(const volatile int *)&c->err;
-    if (e != 0) atomicCAS(sticky, 0, e);
 }
 
 void free_split(Split &s) {
@@ -96,11 +34,13 @@ dsssp_status ensure_split(dsssp_graph *g, double delta, cudaStream_t st, Split *
             return DSSSP_OK;
         }
     }
-    Split *slot = &g->splits[0];
+    // a free slot, else the least recently used split that no batch holds
+    Split *slot = nullptr;
     for (auto &s : g->splits) {
         if (!s.valid) { slot = &s; break; }
-        if (s.last_use < slot->last_use) slot = &s;
+        if (s.pins == 0 && (!slot || s.last_use < slot->last_use)) slot = &s;
     }
+    if (!slot) return DSSSP_ERR_UNSUPPORTED;
     if (slot->valid) {
         DSSSP_TRY(cudaStreamSynchronize(st));
         free_split(*slot);
@@ -127,6 +67,15 @@ dsssp_status ensure_split(dsssp_graph *g, double delta, cudaStream_t st, Split *
     slot->last_use = g->use_clock;
     *out = slot;
     return DSSSP_OK;
+}
+
+}  // namespace dsssp
+
+namespace {
+
+__global__ void k_sticky(const Ctl *c, int32_t *sticky) {
+    int e = *(const volatile int *)&c->err;
+    if (e != 0) atomicCAS(sticky, 0, e);
 }
 
 dsssp_status ensure_workspace(dsssp_graph *g) {
@@ -215,6 +164,7 @@ const char *dsssp_status_string(dsssp_status s) {
     case DSSSP_ERR_OOM: return "out of device memory";
     case DSSSP_ERR_UNSUPPORTED: return "unsupported device or launch shape";
     case DSSSP_ERR_TOO_LARGE: return "graph exceeds the fixed working memory of the no-allocation solve";
+    case DSSSP_ERR_DEGENERATE: return "predecessor graph has a cycle (zero-weight ties): gradient undefined";
     }
     return "unknown status";
 }

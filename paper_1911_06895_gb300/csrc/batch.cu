@@ -1,0 +1,1086 @@
+// batch.cu -- many delta-stepping solves in one persistent launch, and the
+// adjoint of their distances with respect to the weights.
+//
+// Forward (k_batch). Every block is a team that takes instances (source,
+// graph) from a device-side queue and runs each one start to end, with its own
+// bucket state in its own slice of the working memory. The phases of one
+// instance are those of Fig. 1 (Sections III-C, III-D, IV-C):
+//   LIGHT   relax the light arcs of the frontier F (the vertices of bucket i
+//           whose distance changed in the previous round): t_Req = A_L^T (t o t_Bi),
+//           with the re-introduction filter and t = min(t, t_Req) fused into one
+//           64-bit atomicMin per arc on packed[v] = key(t[v]) << 32 | low word;
+//   HEAVY   relax the heavy arcs of S, the vertices processed in bucket i:
+//           t_Req = A_H^T (t o S);
+//   SELECT  the next non-empty bucket: the far list (vertices whose distance
+//           fell into a later bucket) is scanned once; vertices of the new
+//           bucket i go to F and S, those of later buckets stay, those of
+//           processed buckets are dropped.
+// A team's phases are separated by block barriers only, so a phase costs a few
+// dependent memory round trips; the other teams keep the memory system busy.
+// The low word of packed[] is the predecessor vertex, or -- with a tape -- the
+// split position of the arc that realised the distance. Rows occupy ascending
+// split positions, so the minimum over (key, position) selects the same
+// predecessor as the minimum over (key, vertex).
+//
+// Adjoint (k_backward). With L = sum_v c[v] * d[v] and d[v] the sum of the
+// tree-path weights, dL/dw(e) for the tree arc e = (pred[v], v) is the sum of c
+// over the subtree below v. The subtree sums are taken leaves first: a vertex
+// is ready once all of its tree children have added their sums to it, so each
+// round's ready list depends only on earlier rounds (a topological order of
+// the predecessor tree, whatever order the forward run found the distances in).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "graph.cuh"
+#include "warp_util.cuh"
+
+namespace dsssp {
+namespace {
+
+using wu::FULL;
+using wu::inf_key;
+using wu::key_add;
+using wu::lane_id;
+
+constexpr int kTeamThreads = 512;
+constexpr int kTeamWarps = kTeamThreads / 32;
+constexpr int kTIlp = 2;                    // independent 32-arc steps per warp iteration
+constexpr uint32_t kTMinSlice = 32u * kTIlp;
+constexpr uint32_t NONE = 0xFFFFFFFFu;
+
+enum TMode : uint32_t { T_LIGHT = 0, T_HEAVY = 1, T_SELECT = 2, T_DONE = 3 };
+
+enum BStat {
+    BS_BUCKETS = 0, BS_LIGHT, BS_HEAVY, BS_SELECT, BS_ALIGHT, BS_AHEAVY, BS_IMPROVE, BS_FARSCAN, BS_NS, BS_TEAM,
+    kBStats = 16
+};
+
+struct BGraphDev {
+    const uint4 *vinfo;        // n: (light begin, light end = heavy begin, heavy end, 0)
+    const uint2 *arcs;         // m: (head, weight bits), light first per row
+    const uint32_t *perm;      // m: split position -> input arc index
+    const uint32_t *tail;      // m: split position -> row (tape only)
+    double delta;
+    uint32_t n, m;
+};
+
+struct BInstDev {
+    void *dist;                // n of the graph's dtype
+    int32_t *pred;             // n, or null
+    uint32_t *tree;            // tape: input index of v's tree arc (NONE: source / unreached)
+    uint32_t *parent;          // tape: pred[v] (NONE: unreached)
+    uint32_t graph, src, orig, pad;
+};
+
+// Per-team working memory: array x of team t starts at x + t * cap.
+struct TeamWS {
+    unsigned long long *packed;
+    uint32_t *nstamp;          // phase stamp of the last push into the next frontier
+    uint32_t *sstamp;          // S-round stamp of the last push into S
+    uint32_t *fflag;           // instance stamp while the vertex has a far-list entry
+    uint2 *F0, *F1, *S0, *S1;  // (vertex, exclusive arc offset)
+    uint32_t *X0, *X1;         // far lists
+};
+
+struct BatchArgs {
+    const BGraphDev *graphs;
+    const BInstDev *inst;      // in queue order
+    uint32_t n_inst;
+    uint32_t pad0;
+    uint32_t *queue;           // next instance (reset before every launch)
+    uint32_t *gen;             // per team: stamp generator, kept across launches
+    int *err;                  // first device-side status
+    long long *stats;          // n_inst x kBStats, indexed by the caller's instance order
+    TeamWS ws;
+    unsigned long long cap;    // vertices per team slice
+    long long max_phases;
+};
+
+// Destinations and thresholds of one phase (uniform over the block).
+struct Ph {
+    uint2 *Fo;
+    unsigned long long *cF;
+    uint2 *So;
+    unsigned long long *cS;
+    uint32_t *Xo;
+    uint32_t *cX;
+    uint32_t T, T_lo, pstamp, sst, fst;
+};
+
+// Team control in shared memory. Thread 0 decides the next phase between two
+// block barriers; every thread then reads the decision.
+struct TeamShared {
+    BInstDev I;                              // the instance being solved and its graph
+    BGraphDev G;
+    Ph ph;                                   // the current phase's destinations
+    uint32_t *nstamp, *sstamp, *fflag;
+    unsigned long long ctrF[2], ctrS[2];     // (entries << 32) | arcs
+    unsigned long long a_light, a_heavy, improve, far_scanned;
+    long long phases, n_light, n_heavy, n_select, buckets;
+    unsigned long long t0;
+    uint32_t nX[2];
+    uint32_t far_min;                        // <= every key of a live far entry
+    uint32_t next_min;                       // SELECT: smallest key kept
+    uint32_t mode, cur, scur, xcur, pstamp, sst, T, T_lo, fst, gen, inst;
+};
+
+struct TStage {
+    uint32_t fv[64], fd[64];   // next frontier (vertex, light degree)
+    uint32_t sv[64], sd[64];   // S (vertex, heavy degree)
+    uint32_t xv[64];           // far list
+};
+
+struct Team {
+    const uint4 *vinfo;
+    const uint2 *arcs;
+    unsigned long long *packed;
+    uint32_t n, m;
+};
+
+struct TPush {
+    bool f, s, x;
+    uint32_t fdeg, sdeg;
+};
+
+__device__ __forceinline__ void stage_push(const Ph &ph, TStage &ws, uint32_t &nf, uint32_t &ns, uint32_t &nx,
+                                           const TPush &p, uint32_t v) {
+    if (__ballot_sync(FULL, p.f || p.s || p.x) == 0u) return;
+    wu::stage_arc_entry(p.f, v, p.fdeg, ws.fv, ws.fd, nf, ph.Fo, ph.cF);
+    wu::stage_arc_entry(p.s, v, p.sdeg, ws.sv, ws.sd, ns, ph.So, ph.cS);
+    wu::stage_id(p.x, v, ws.xv, nx, ph.Xo, ph.cX);
+}
+
+__device__ __forceinline__ void drain_push(const Ph &ph, TStage &ws, uint32_t &nf, uint32_t &ns, uint32_t &nx) {
+    if (nf) wu::flush_arc_entries(ws.fv, ws.fd, nf, ph.Fo, ph.cF);
+    if (ns) wu::flush_arc_entries(ws.sv, ws.sd, ns, ph.So, ph.cS);
+    if (nx) wu::flush_ids(ws.xv, nx, ph.Xo, ph.cX);
+    __syncwarp();
+    nf = ns = nx = 0u;
+}
+
+// relax(v, new distance) of Section III-C after a strict decrease of t[v]:
+// back into bucket i (once per phase into F, once per S round into S), or
+// into a later bucket (once into the far list while it has a live entry).
+template <int DT>
+__device__ __forceinline__ void on_improved(const Team &t, const TeamShared &s, uint32_t v, uint32_t ck, TPush &p,
+                                            uint32_t &far_min) {
+    const Ph &ph = s.ph;
+    if (ck < ph.T) {
+        const uint32_t prev = atomicExch(s.nstamp + v, ph.pstamp);
+        const uint4 vi = t.vinfo[v];
+        const uint32_t ss = __ldcg(s.sstamp + v);
+        if (prev == ph.pstamp) return;
+        p.fdeg = vi.y - vi.x;
+        p.f = p.fdeg != 0u;
+        if (ss != ph.sst) {
+            s.sstamp[v] = ph.sst;
+            p.sdeg = vi.z - vi.y;
+            p.s = p.sdeg != 0u;
+        }
+    } else {
+        far_min = min(far_min, ck);
+        p.x = atomicExch(s.fflag + v, ph.fst) != ph.fst;
+    }
+}
+
+// LIGHT / HEAVY: relax the arcs of one list, split evenly over the team's warps
+// (merge-path over the entries' arc offsets; 32-entry window per warp).
+template <int DT, bool LIGHT, bool TAPE>
+__device__ void team_relax(const Team &t, const TeamShared &s, const uint2 *list, uint32_t count, uint32_t E,
+                           TStage &ws, int *sl, uint32_t &far_min, unsigned long long &improved,
+                           unsigned long long &relaxed) {
+    const Ph &ph = s.ph;
+    const uint32_t lane = lane_id();
+    const uint32_t gw = threadIdx.x >> 5, nw_all = blockDim.x >> 5;
+    const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[2 * j]
+    uint32_t nf = 0, ns = 0, nx = 0;
+    const uint32_t want_w = (E + kTMinSlice - 1u) / kTMinSlice;
+    const uint32_t nw = want_w < nw_all ? want_w : nw_all;
+    if (gw < nw) {
+        const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
+        const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
+        // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
+        uint32_t lo = 0, hi = count;
+        while (hi - lo > 32u) {
+            const uint32_t step = (hi - lo + 31u) >> 5;
+            const uint32_t q = lo + lane * step;
+            const bool ok = q < hi && __ldcg(offs + 2ull * q) <= e0;
+            lo += (31u - __clz(__ballot_sync(FULL, ok))) * step;
+            hi = min(hi, lo + step);
+        }
+        {
+            const uint32_t q = lo + lane;
+            const bool ok = q < hi && __ldcg(offs + 2ull * q) <= e0;
+            lo += 31u - __clz(__ballot_sync(FULL, ok));
+        }
+        // window: lane k holds entry jw + k; wend = arc offset just past the window
+        uint32_t jw = lo, wv = 0, woff = 0xFFFFFFFFu, wbeg = 0, wkey = inf_key<DT>(), wend = 0;
+        auto load_window = [&](uint32_t j) {
+            const uint32_t idx = j + lane;
+            if (idx < count) {
+                const uint2 en = __ldcg(list + idx);
+                wv = en.x < t.n ? en.x : 0u;
+                woff = en.y;
+                wkey = (uint32_t)(__ldcg(t.packed + wv) >> 32);
+                const uint4 vi = t.vinfo[wv];
+                wbeg = LIGHT ? vi.x : vi.y;
+            } else {
+                wv = 0; woff = 0xFFFFFFFFu; wbeg = 0; wkey = inf_key<DT>();
+            }
+            wend = (j + 32u < count) ? __ldcg(offs + 2ull * (j + 32u)) : E;
+        };
+        load_window(jw);
+        int *own_map = sl + gw * 32;
+        for (uint32_t base0 = e0; base0 < e1; base0 += 32u * kTIlp) {
+            uint32_t ai[kTIlp], ov[kTIlp], okey[kTIlp];
+            bool ok[kTIlp];
+            #pragma unroll
+            for (int k = 0; k < kTIlp; ++k) {
+                const uint32_t base = base0 + 32u * (uint32_t)k;
+                ok[k] = false;
+                ai[k] = 0u;
+                ov[k] = 0u;
+                okey[k] = inf_key<DT>();
+                if (base < e1) {
+                    const uint32_t last = min(base + 31u, e1 - 1u);
+                    if (last >= wend) {
+                        const uint32_t shift = base >= wend ? 32u : 31u - __clz(__ballot_sync(FULL, woff <= base));
+                        jw += shift;
+                        load_window(jw);
+                    }
+                    // owner of arc base + lane: the last window entry starting at or before it
+                    const int carry = 31 - __clz(__ballot_sync(FULL, woff <= base));
+                    const uint32_t next_off = __shfl_sync(FULL, woff, (carry + 1) & 31);
+                    const bool one_owner = carry == 31 ? wend > base + 31u : next_off > base + 31u;
+                    int own = carry;
+                    if (!one_owner) {
+                        own_map[lane] = -1;
+                        __syncwarp();
+                        if (woff > base && woff - base < 32u) own_map[woff - base] = (int)lane;
+                        __syncwarp();
+                        own = own_map[lane];
+                        #pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const int x = __shfl_up_sync(FULL, own, o);
+                            if ((int)lane >= o) own = max(own, x);
+                        }
+                        own = max(own, carry);
+                        __syncwarp();
+                    }
+                    ov[k] = __shfl_sync(FULL, wv, own);
+                    const uint32_t ooff = __shfl_sync(FULL, woff, own);
+                    const uint32_t obeg = __shfl_sync(FULL, wbeg, own);
+                    okey[k] = __shfl_sync(FULL, wkey, own);
+                    const uint32_t e = base + lane;
+                    ai[k] = obeg + (e - ooff);
+                    ok[k] = e < e1 && ai[k] < t.m && okey[k] < inf_key<DT>();
+                }
+            }
+            uint2 arc[kTIlp];
+            #pragma unroll
+            for (int k = 0; k < kTIlp; ++k) arc[k] = ok[k] ? __ldcs(t.arcs + ai[k]) : make_uint2(0u, 0u);
+            uint32_t ck[kTIlp];
+            unsigned long long cur[kTIlp], cand[kTIlp];
+            #pragma unroll
+            for (int k = 0; k < kTIlp; ++k) {
+                ck[k] = ok[k] ? key_add<DT>(okey[k], arc[k].y) : inf_key<DT>();
+                cand[k] = ((unsigned long long)ck[k] << 32) | (TAPE ? ai[k] : ov[k]);
+                cur[k] = ck[k] < inf_key<DT>() ? __ldcg(t.packed + arc[k].x) : 0ull;
+            }
+            // packed[v] only decreases: a value read earlier bounds it, so the
+            // atomic is skipped when the request cannot win (old = 0: no win)
+            unsigned long long old[kTIlp];
+            #pragma unroll
+            for (int k = 0; k < kTIlp; ++k)
+                old[k] = (ck[k] < inf_key<DT>() && cand[k] < cur[k]) ? atomicMin(t.packed + arc[k].x, cand[k]) : 0ull;
+            #pragma unroll
+            for (int k = 0; k < kTIlp; ++k) {
+                TPush p{};
+                if (cand[k] < old[k] && (uint32_t)(old[k] >> 32) > ck[k]) {      // strict distance decrease
+                    ++improved;
+                    on_improved<DT>(t, s, arc[k].x, ck[k], p, far_min);
+                }
+                stage_push(ph, ws, nf, ns, nx, p, arc[k].x);
+            }
+        }
+        if (lane == 0) relaxed += e1 - e0;
+    }
+    drain_push(ph, ws, nf, ns, nx);
+}
+
+// SELECT: one pass over the far list with the new bucket's bounds [T_lo, T).
+template <int DT>
+__device__ void team_select(const Team &t, const TeamShared &s, const uint32_t *xin, uint32_t count, TStage &ws,
+                            uint32_t &next_min) {
+    const Ph &ph = s.ph;
+    const uint32_t lane = lane_id();
+    const uint32_t gw = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t nf = 0, ns = 0, nx = 0;
+    for (uint32_t base = gw * 32u; base < count; base += nw * 32u) {
+        const uint32_t idx = base + lane;
+        TPush p{};
+        uint32_t v = NONE;
+        if (idx < count && (v = __ldcs(xin + idx)) < t.n) {
+            const uint32_t k = (uint32_t)(__ldcg(t.packed + v) >> 32);
+            if (k < ph.T_lo) {
+                s.fflag[v] = 0u;                     // its bucket was processed
+            } else if (k < ph.T) {
+                s.fflag[v] = 0u;                     // B_i of the new bucket: F and S
+                const uint4 vi = t.vinfo[v];
+                p.fdeg = vi.y - vi.x;
+                p.f = p.fdeg != 0u;
+                s.sstamp[v] = ph.sst;
+                p.sdeg = vi.z - vi.y;
+                p.s = p.sdeg != 0u;
+            } else {
+                p.x = true;                          // a later bucket: stays
+                next_min = min(next_min, k);
+            }
+        }
+        stage_push(ph, ws, nf, ns, nx, p, v);
+    }
+    drain_push(ph, ws, nf, ns, nx);
+}
+
+__device__ __forceinline__ uint32_t warp_min(uint32_t x) { return __reduce_min_sync(FULL, x); }
+
+__device__ __forceinline__ unsigned long long warp_sum(unsigned long long x) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+    return x;
+}
+
+// The control flow of Fig. 1 for one instance (thread 0, between barriers).
+template <int DT>
+__device__ __noinline__ void team_decide(TeamShared &s, const BGraphDev &g, const BatchArgs &a) {
+    switch (s.mode) {
+    case T_LIGHT:
+        s.n_light += 1;
+        s.ctrF[s.cur] = 0ull;
+        s.cur ^= 1u;
+        break;
+    case T_HEAVY:
+        s.n_heavy += 1;
+        s.ctrS[s.scur] = 0ull;
+        s.scur ^= 1u;                        // S pushed during the heavy pass (re-opened bucket)
+        s.cur ^= 1u;
+        break;
+    case T_SELECT:
+        s.n_select += 1;
+        s.nX[s.xcur] = 0u;
+        s.xcur ^= 1u;
+        s.cur ^= 1u;
+        s.far_min = s.next_min;
+        if ((s.ctrF[s.cur] >> 32) != 0ull || (s.ctrS[s.scur] >> 32) != 0ull) s.buckets += 1;
+        break;
+    default:
+        break;
+    }
+    s.phases += 1;
+    if (s.phases >= a.max_phases) {
+        atomicCAS(a.err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
+        s.mode = T_DONE;
+        return;
+    }
+    s.pstamp = ++s.gen;
+    if ((s.ctrF[s.cur] >> 32) != 0ull) {             // inner loop of Fig. 1: while t_Bi != 0
+        s.mode = T_LIGHT;
+    } else if ((s.ctrS[s.scur] >> 32) != 0ull) {     // bucket settled: heavy pass over S
+        s.mode = T_HEAVY;
+        s.sst = ++s.gen;
+    } else if (s.nX[s.xcur] != 0u) {                 // next non-empty bucket
+        s.mode = T_SELECT;
+        s.T_lo = s.T;
+        if (s.far_min < inf_key<DT>()) {
+            const int64_t i = bucket_of_key(s.far_min, DT, g.delta);
+            s.T = i < INT64_MAX ? bucket_floor_key(i + 1, DT, g.delta) : inf_key<DT>();
+        } else {
+            s.T = inf_key<DT>();
+        }
+        s.sst = ++s.gen;
+        s.next_min = inf_key<DT>();
+    } else {
+        s.mode = T_DONE;
+    }
+}
+
+// Destinations of the next phase's pushes (thread 0, after team_decide).
+template <int DT>
+__device__ __noinline__ void set_phase(TeamShared &s, const BatchArgs &a, size_t off) {
+    const uint32_t mode = s.mode, cur = s.cur, scur = s.scur, xcur = s.xcur;
+    Ph &ph = s.ph;
+    ph.Fo = (cur ? a.ws.F0 : a.ws.F1) + off;                 // F[cur ^ 1]
+    ph.cF = &s.ctrF[cur ^ 1u];
+    const uint32_t sp = mode == T_HEAVY ? scur ^ 1u : scur;  // a heavy pass feeds the next S
+    ph.So = (sp ? a.ws.S1 : a.ws.S0) + off;
+    ph.cS = &s.ctrS[sp];
+    const uint32_t xp = mode == T_SELECT ? xcur ^ 1u : xcur; // SELECT rebuilds the far list
+    ph.Xo = (xp ? a.ws.X1 : a.ws.X0) + off;
+    ph.cX = &s.nX[xp];
+    ph.T = s.T;
+    ph.T_lo = s.T_lo;
+    ph.pstamp = s.pstamp;
+    ph.sst = s.sst;
+    ph.fst = s.fst;
+}
+
+template <int DT, bool TAPE>
+__global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
+    __shared__ TeamShared s;
+    __shared__ TStage stage[kTeamWarps];
+    __shared__ int own_map[kTeamWarps * 32];
+    const uint32_t tid = threadIdx.x;
+    const size_t off = (size_t)blockIdx.x * a.cap;
+    Team t;
+    t.packed = a.ws.packed + off;
+    if (tid == 0) {
+        s.gen = a.gen[blockIdx.x];
+        s.nstamp = a.ws.nstamp + off;
+        s.sstamp = a.ws.sstamp + off;
+        s.fflag = a.ws.fflag + off;
+    }
+    for (;;) {
+        if (tid == 0) s.inst = atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const uint32_t ii = s.inst;
+        if (ii >= a.n_inst) break;
+        if (tid == 0) {
+            s.I = a.inst[ii];
+            s.G = a.graphs[s.I.graph];
+        }
+        __syncthreads();
+        t.vinfo = s.G.vinfo;
+        t.arcs = s.G.arcs;
+        t.n = s.G.n;
+        t.m = s.G.m;
+        // stamps restart from 1 before the generator could wrap
+        if (s.gen > 0xF0000000u) {
+            for (size_t v = tid; v < a.cap; v += blockDim.x) { s.nstamp[v] = 0u; s.sstamp[v] = 0u; s.fflag[v] = 0u; }
+            __syncthreads();
+            if (tid == 0) s.gen = 1u;
+        }
+        const unsigned long long init = ((unsigned long long)inf_key<DT>() << 32) | NONE;
+        for (uint32_t v = tid; v < t.n; v += blockDim.x) t.packed[v] = init;
+        __syncthreads();
+        if (tid == 0) {
+            s.t0 = wu::globaltimer();
+            s.ctrF[0] = s.ctrF[1] = s.ctrS[0] = s.ctrS[1] = 0ull;
+            s.a_light = s.a_heavy = s.improve = s.far_scanned = 0ull;
+            s.phases = s.n_light = s.n_heavy = s.n_select = 0;
+            s.buckets = 1;
+            s.nX[0] = s.nX[1] = 0u;
+            s.far_min = inf_key<DT>();
+            s.next_min = inf_key<DT>();
+            s.cur = s.scur = s.xcur = 0u;
+            s.fst = ++s.gen;
+            s.sst = ++s.gen;
+            s.pstamp = ++s.gen;
+            s.T_lo = 0u;
+            s.T = bucket_floor_key(1, DT, s.G.delta);    // bucket 0 holds the source
+            const uint32_t src = s.I.src;
+            t.packed[src] = TAPE ? (unsigned long long)NONE : (unsigned long long)src;   // key 0
+            const uint4 vi = s.G.vinfo[src];
+            if (vi.y > vi.x) {
+                a.ws.F0[off] = make_uint2(src, 0u);
+                s.ctrF[0] = (1ull << 32) | (vi.y - vi.x);
+            }
+            if (vi.z > vi.y) {
+                a.ws.S0[off] = make_uint2(src, 0u);
+                s.ctrS[0] = (1ull << 32) | (vi.z - vi.y);
+            }
+            s.sstamp[src] = s.sst;
+            s.mode = (s.ctrF[0] >> 32) ? T_LIGHT : ((s.ctrS[0] >> 32) ? T_HEAVY : T_DONE);
+            if (s.mode == T_HEAVY) s.sst = ++s.gen;
+        }
+        __syncthreads();
+        if (tid == 0) set_phase<DT>(s, a, off);
+        __syncthreads();
+        for (;;) {
+            const uint32_t mode = s.mode;
+            if (mode == T_DONE) break;
+            uint32_t fmin = inf_key<DT>();
+            unsigned long long improved = 0, relaxed = 0;
+            TStage &ws = stage[tid >> 5];
+            if (mode == T_LIGHT) {
+                const unsigned long long c = s.ctrF[s.cur];
+                team_relax<DT, true, TAPE>(t, s, (s.cur ? a.ws.F1 : a.ws.F0) + off, (uint32_t)(c >> 32), (uint32_t)c,
+                                           ws, own_map, fmin, improved, relaxed);
+            } else if (mode == T_HEAVY) {
+                const unsigned long long c = s.ctrS[s.scur];
+                team_relax<DT, false, TAPE>(t, s, (s.scur ? a.ws.S1 : a.ws.S0) + off, (uint32_t)(c >> 32),
+                                            (uint32_t)c, ws, own_map, fmin, improved, relaxed);
+            } else {
+                team_select<DT>(t, s, (s.xcur ? a.ws.X1 : a.ws.X0) + off, s.nX[s.xcur], ws, fmin);
+            }
+            fmin = warp_min(fmin);
+            improved = warp_sum(improved);
+            if (lane_id() == 0) {
+                if (fmin < inf_key<DT>()) atomicMin(mode == T_SELECT ? &s.next_min : &s.far_min, fmin);
+                if (improved) atomicAdd(&s.improve, improved);
+                if (relaxed) atomicAdd(mode == T_LIGHT ? &s.a_light : &s.a_heavy, relaxed);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                if (mode == T_SELECT) s.far_scanned += s.nX[s.xcur];
+                team_decide<DT>(s, s.G, a);
+                set_phase<DT>(s, a, off);
+            }
+            __syncthreads();
+        }
+        // unpack: dist = key bits; pred from the low word (tape: via the arc's row)
+        {
+            const BInstDev &I = s.I;
+            const BGraphDev &G = s.G;
+            const uint32_t src = I.src;
+            uint32_t *dist = reinterpret_cast<uint32_t *>(I.dist);
+            for (uint32_t v = tid; v < t.n; v += blockDim.x) {
+                const unsigned long long p = __ldcg(t.packed + v);
+                const uint32_t key = (uint32_t)(p >> 32), low = (uint32_t)p;
+                const bool reached = key < inf_key<DT>();
+                uint32_t pr = NONE, tree = NONE;
+                if (reached) {
+                    if (v == src) pr = src;
+                    else if (TAPE) { pr = low < t.m ? G.tail[low] : NONE; tree = low < t.m ? G.perm[low] : NONE; }
+                    else pr = low;
+                }
+                dist[v] = key;
+                if (I.pred) I.pred[v] = (int32_t)pr;
+                if (TAPE) {
+                    I.tree[v] = tree;
+                    I.parent[v] = pr;
+                }
+            }
+        }
+        if (tid == 0) {
+            long long *st = a.stats + (size_t)s.I.orig * kBStats;
+            st[BS_BUCKETS] = s.buckets;
+            st[BS_LIGHT] = s.n_light;
+            st[BS_HEAVY] = s.n_heavy;
+            st[BS_SELECT] = s.n_select;
+            st[BS_ALIGHT] = (long long)s.a_light;
+            st[BS_AHEAVY] = (long long)s.a_heavy;
+            st[BS_IMPROVE] = (long long)s.improve;
+            st[BS_FARSCAN] = (long long)s.far_scanned;
+            st[BS_NS] = (long long)(wu::globaltimer() - s.t0);
+            st[BS_TEAM] = blockIdx.x;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) a.gen[blockIdx.x] = s.gen;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint.
+
+struct BwdArgs {
+    const BGraphDev *graphs;
+    const BInstDev *inst;      // queue order
+    uint32_t n_inst;
+    uint32_t pad0;
+    uint32_t *queue;
+    int *err;
+    const float *const *c;     // by the caller's instance order
+    double *const *grad64;     // per graph, input arc order
+    TeamWS ws;
+    unsigned long long cap;
+};
+
+__global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
+    __shared__ uint32_t s_inst, s_n[2], s_reached, s_done;
+    const uint32_t tid = threadIdx.x;
+    const size_t off = (size_t)blockIdx.x * a.cap;
+    double *acc = reinterpret_cast<double *>(a.ws.packed + off);     // subtree sums
+    uint32_t *L[2] = {reinterpret_cast<uint32_t *>(a.ws.F0 + off), reinterpret_cast<uint32_t *>(a.ws.F0 + off) + a.cap};
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws.F1 + off);     // children not yet summed
+    for (;;) {
+        if (tid == 0) s_inst = atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const uint32_t ii = s_inst;
+        if (ii >= a.n_inst) break;
+        const BInstDev I = a.inst[ii];
+        const uint32_t n = a.graphs[I.graph].n, m = a.graphs[I.graph].m;
+        const float *c = a.c[I.orig];
+        double *g64 = a.grad64[I.graph];
+        for (uint32_t v = tid; v < n; v += blockDim.x) { acc[v] = 0.0; cnt[v] = 0u; }
+        if (tid == 0) { s_n[0] = s_n[1] = 0u; s_reached = 0u; s_done = 0u; }
+        __syncthreads();
+        uint32_t reached = 0;
+        for (uint32_t v = tid; v < n; v += blockDim.x) {
+            const uint32_t p = I.parent[v];
+            if (p == NONE) continue;
+            ++reached;
+            if (v != I.src && p < n) atomicAdd(cnt + p, 1u);
+        }
+        reached = __reduce_add_sync(FULL, reached);
+        if (lane_id() == 0 && reached) atomicAdd(&s_reached, reached);
+        __syncthreads();
+        for (uint32_t v = tid; v < n; v += blockDim.x)       // leaves
+            if (I.parent[v] != NONE && __ldcg(cnt + v) == 0u) L[0][atomicAdd(&s_n[0], 1u)] = v;
+        __syncthreads();
+        uint32_t cur = 0, done = 0;
+        while (s_n[cur] != 0u) {
+            const uint32_t cnt_cur = s_n[cur];
+            for (uint32_t k = tid; k < cnt_cur; k += blockDim.x) {
+                const uint32_t v = __ldcg(L[cur] + k);
+                const double sum = __ldcg(acc + v) + (double)c[v];
+                ++done;
+                if (v == I.src) continue;
+                const uint32_t e = I.tree[v], p = I.parent[v];
+                if (e < m) atomicAdd(g64 + e, sum);
+                if (p < n) {
+                    atomicAdd(acc + p, sum);
+                    if (atomicSub(cnt + p, 1u) == 1u) L[cur ^ 1u][atomicAdd(&s_n[cur ^ 1u], 1u)] = p;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) s_n[cur] = 0u;
+            cur ^= 1u;
+            __syncthreads();
+        }
+        done = __reduce_add_sync(FULL, done);
+        if (lane_id() == 0 && done) atomicAdd(&s_done, done);
+        __syncthreads();
+        if (tid == 0 && s_done != s_reached) atomicCAS(a.err, 0, (int)DSSSP_ERR_DEGENERATE);   // a cycle
+        __syncthreads();
+    }
+}
+
+__global__ void k_grad_out(double *const *grad64, float *const *grad_w, const uint32_t *m_of, int accumulate) {
+    const uint32_t gi = blockIdx.y;
+    const uint32_t m = m_of[gi];
+    const double *src = grad64[gi];
+    float *dst = grad_w[gi];
+    for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+        const float g = (float)src[e];
+        dst[e] = accumulate ? dst[e] + g : g;
+    }
+}
+
+// row of every split position (tape: the parent of a tree arc)
+__global__ void k_tail(const uint4 *vinfo, uint32_t n, uint32_t *tail) {
+    const uint32_t lane = lane_id();
+    const uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = w; u < n; u += nw) {
+        const uint4 vi = vinfo[u];
+        for (uint32_t p = vi.x + lane; p < vi.z; p += 32u) tail[p] = u;
+    }
+}
+
+}  // namespace
+}  // namespace dsssp
+
+using namespace dsssp;
+
+// ---------------------------------------------------------------------------
+// Host side.
+
+struct dsssp_batch {
+    int device = 0;
+    int dtype = 0;
+    bool tape = false;
+    bool ran = false;
+    int32_t n_graphs = 0, n_inst = 0;
+    std::vector<dsssp_graph *> graphs;
+    std::vector<Split *> splits;
+    std::vector<uint32_t> m_of;
+    uint32_t teams = 0;
+    unsigned long long cap = 0;
+    void *mem = nullptr;                    // one device allocation for everything below
+    BGraphDev *d_graphs = nullptr;
+    BInstDev *d_inst = nullptr;
+    uint32_t *d_queue = nullptr;            // [0] forward, [1] backward
+    uint32_t *d_gen = nullptr;
+    int *d_err = nullptr;
+    long long *d_stats = nullptr;
+    uint32_t *d_tail = nullptr;             // tape: per graph, m entries
+    uint32_t *d_tape = nullptr;             // tape: per instance, tree + parent
+    double *d_grad64 = nullptr;             // tape: per graph, m entries
+    double **d_grad64_ptr = nullptr;
+    float **d_gradw_ptr = nullptr;
+    const float **d_c_ptr = nullptr;
+    uint32_t *d_m_of = nullptr;
+    TeamWS ws{};
+    BatchArgs args{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void *h_ptrs = nullptr;                 // pinned staging for backward pointer tables
+    long long max_phases = 0;
+};
+
+namespace {
+
+void release(dsssp_batch *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->mem);
+    if (b->h_ptrs) cudaFreeHost(b->h_ptrs);
+    for (Split *s : b->splits)
+        if (s && s->pins > 0) s->pins--;
+    delete b;
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, const double *delta, int32_t n_inst,
+                                const int32_t *src, const int32_t *src_graph, void *const *dist,
+                                int32_t *const *pred, uint32_t flags, const dsssp_options *opt, void *stream,
+                                dsssp_batch **out) {
+    if (!out) return DSSSP_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!graphs || n_graphs < 1 || !delta || n_inst < 1 || !src || !dist) return DSSSP_ERR_INVALID_ARG;
+    if (flags & ~DSSSP_BATCH_TAPE) return DSSSP_ERR_INVALID_ARG;
+    dsssp_options o;
+    dsssp_options_default(&o);
+    if (opt) {
+        if (opt->struct_size != sizeof(dsssp_options)) return DSSSP_ERR_INVALID_ARG;
+        if (opt->block_size && opt->block_size != kTeamThreads) return DSSSP_ERR_INVALID_ARG;
+        if (opt->grid_size < 0 || opt->max_phases < 0) return DSSSP_ERR_INVALID_ARG;
+        if (opt->grid_size) o.grid_size = opt->grid_size;
+        if (opt->max_phases) o.max_phases = opt->max_phases;
+    }
+    const int dtype = graphs[0] ? graphs[0]->dtype : -1;
+    const int device = graphs[0] ? graphs[0]->device : -1;
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        if (!graphs[i] || graphs[i]->dtype != dtype || graphs[i]->device != device) return DSSSP_ERR_INVALID_ARG;
+        if (!(delta[i] > 0.0)) return DSSSP_ERR_INVALID_ARG;
+    }
+    const bool tape = (flags & DSSSP_BATCH_TAPE) != 0;
+    if (tape && dtype != DSSSP_F32) return DSSSP_ERR_UNSUPPORTED;
+    for (int32_t k = 0; k < n_inst; ++k) {
+        const int32_t gi = src_graph ? src_graph[k] : 0;
+        if (gi < 0 || gi >= n_graphs) return DSSSP_ERR_INVALID_ARG;
+        if (src[k] < 0 || (int64_t)src[k] >= graphs[gi]->n || !dist[k]) return DSSSP_ERR_INVALID_ARG;
+    }
+    DeviceGuard dg(device);
+    cudaStream_t st = (cudaStream_t)stream;
+    dsssp_batch *b = new (std::nothrow) dsssp_batch();
+    if (!b) return DSSSP_ERR_OOM;
+    b->device = device;
+    b->dtype = dtype;
+    b->tape = tape;
+    b->n_graphs = n_graphs;
+    b->n_inst = n_inst;
+    b->max_phases = o.max_phases;
+    b->graphs.assign(graphs, graphs + n_graphs);
+    auto fail = [&](dsssp_status s) {
+        release(b);
+        return s;
+    };
+    // splits (pinned while the plan lives)
+    b->splits.assign(n_graphs, nullptr);
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        Split *sp = nullptr;
+        dsssp_status rc = ensure_split(graphs[i], delta[i], st, &sp);
+        if (rc != DSSSP_OK) return fail(rc);
+        sp->pins++;
+        b->splits[i] = sp;
+    }
+    // teams: resident blocks, no more than instances, working memory within half of what is free
+    int bps = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &bps, dtype == DSSSP_F32 ? (tape ? (const void *)k_batch<DSSSP_F32, true> : (const void *)k_batch<DSSSP_F32, false>)
+                                 : (const void *)k_batch<DSSSP_I32, false>,
+        kTeamThreads, 0);
+    if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return fail(DSSSP_ERR_CUDA);
+    if (bps < 1) return fail(DSSSP_ERR_UNSUPPORTED);
+    unsigned long long cap = 1;
+    size_t sum_m = 0, sum_n_inst = 0;
+    b->m_of.resize(n_graphs);
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        cap = std::max<unsigned long long>(cap, (unsigned long long)graphs[i]->n);
+        b->m_of[i] = (uint32_t)graphs[i]->m;
+        sum_m += (size_t)graphs[i]->m;
+    }
+    for (int32_t k = 0; k < n_inst; ++k) sum_n_inst += (size_t)graphs[src_graph ? src_graph[k] : 0]->n;
+    const size_t per_team = (size_t)cap * (8 + 4 + 4 + 4 + 8 * 4 + 4 * 2);
+    long long teams = (long long)bps * sms;
+    if (o.grid_size) teams = std::min<long long>(teams, o.grid_size);
+    teams = std::min<long long>(teams, n_inst);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && per_team > 0)
+        teams = std::max<long long>(1, std::min<long long>(teams, (long long)((free_b / 2) / per_team)));
+    b->teams = (uint32_t)teams;
+    b->cap = cap;
+    // one allocation: tables, counters, per-team memory, tape
+    size_t bytes = 0;
+    const size_t o_graphs = bytes; bytes += up256(sizeof(BGraphDev) * n_graphs);
+    const size_t o_inst = bytes;   bytes += up256(sizeof(BInstDev) * n_inst);
+    const size_t o_queue = bytes;  bytes += up256(2 * sizeof(uint32_t));
+    const size_t o_gen = bytes;    bytes += up256(sizeof(uint32_t) * teams);
+    const size_t o_err = bytes;    bytes += up256(sizeof(int));
+    const size_t o_stats = bytes;  bytes += up256(sizeof(long long) * kBStats * n_inst);
+    const size_t o_mof = bytes;    bytes += up256(sizeof(uint32_t) * n_graphs);
+    const size_t o_ws = bytes;     bytes += up256(per_team * teams + 10 * 256);
+    size_t o_tail = 0, o_tape = 0, o_g64 = 0, o_g64p = 0, o_gwp = 0, o_cp = 0;
+    if (tape) {
+        o_tail = bytes; bytes += up256(sizeof(uint32_t) * std::max<size_t>(sum_m, 1));
+        o_tape = bytes; bytes += up256(sizeof(uint32_t) * 2 * sum_n_inst);
+        o_g64 = bytes;  bytes += up256(sizeof(double) * std::max<size_t>(sum_m, 1));
+        o_g64p = bytes; bytes += up256(sizeof(double *) * n_graphs);
+        o_gwp = bytes;  bytes += up256(sizeof(float *) * n_graphs);
+        o_cp = bytes;   bytes += up256(sizeof(float *) * n_inst);
+    }
+    char *mem = nullptr;
+    if ((e = cudaMalloc(&mem, bytes)) != cudaSuccess) return fail(cuda_status(e));
+    b->mem = mem;
+    b->d_graphs = (BGraphDev *)(mem + o_graphs);
+    b->d_inst = (BInstDev *)(mem + o_inst);
+    b->d_queue = (uint32_t *)(mem + o_queue);
+    b->d_gen = (uint32_t *)(mem + o_gen);
+    b->d_err = (int *)(mem + o_err);
+    b->d_stats = (long long *)(mem + o_stats);
+    b->d_m_of = (uint32_t *)(mem + o_mof);
+    {
+        char *w = mem + o_ws;
+        auto take = [&](size_t each) {
+            char *p = w;
+            w += up256(each * cap * teams);
+            return p;
+        };
+        b->ws.packed = (unsigned long long *)take(8);
+        b->ws.nstamp = (uint32_t *)take(4);
+        b->ws.sstamp = (uint32_t *)take(4);
+        b->ws.fflag = (uint32_t *)take(4);
+        b->ws.F0 = (uint2 *)take(8);
+        b->ws.F1 = (uint2 *)take(8);
+        b->ws.S0 = (uint2 *)take(8);
+        b->ws.S1 = (uint2 *)take(8);
+        b->ws.X0 = (uint32_t *)take(4);
+        b->ws.X1 = (uint32_t *)take(4);
+    }
+    if (tape) {
+        b->d_tail = (uint32_t *)(mem + o_tail);
+        b->d_tape = (uint32_t *)(mem + o_tape);
+        b->d_grad64 = (double *)(mem + o_g64);
+        b->d_grad64_ptr = (double **)(mem + o_g64p);
+        b->d_gradw_ptr = (float **)(mem + o_gwp);
+        b->d_c_ptr = (const float **)(mem + o_cp);
+        if ((e = cudaMallocHost(&b->h_ptrs, sizeof(void *) * (size_t)(n_graphs + n_inst))) != cudaSuccess)
+            return fail(cuda_status(e));
+    }
+    // tables (host), instances in queue order: largest graphs first
+    std::vector<BGraphDev> hg(n_graphs);
+    std::vector<double *> hg64(n_graphs, nullptr);
+    size_t moff = 0;
+    for (int32_t i = 0; i < n_graphs; ++i) {
+        hg[i].vinfo = b->splits[i]->vinfo;
+        hg[i].arcs = b->splits[i]->arcs;
+        hg[i].perm = b->splits[i]->perm;
+        hg[i].tail = tape ? b->d_tail + moff : nullptr;
+        hg[i].delta = delta[i];
+        hg[i].n = (uint32_t)graphs[i]->n;
+        hg[i].m = (uint32_t)graphs[i]->m;
+        if (tape) hg64[i] = b->d_grad64 + moff;
+        moff += (size_t)graphs[i]->m;
+    }
+    std::vector<int32_t> order(n_inst);
+    std::iota(order.begin(), order.end(), 0);
+    auto gof = [&](int32_t k) { return src_graph ? src_graph[k] : 0; };
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        return graphs[gof(x)]->m + graphs[gof(x)]->n > graphs[gof(y)]->m + graphs[gof(y)]->n;
+    });
+    std::vector<BInstDev> hi(n_inst);
+    std::vector<size_t> tape_off(n_inst, 0);
+    size_t toff = 0;
+    for (int32_t k = 0; k < n_inst; ++k) {
+        tape_off[k] = toff;
+        toff += 2 * (size_t)graphs[gof(k)]->n;
+    }
+    for (int32_t q = 0; q < n_inst; ++q) {
+        const int32_t k = order[q];
+        BInstDev &d = hi[q];
+        d.dist = dist[k];
+        d.pred = pred ? pred[k] : nullptr;
+        d.graph = (uint32_t)gof(k);
+        d.src = (uint32_t)src[k];
+        d.orig = (uint32_t)k;
+        d.tree = tape ? b->d_tape + tape_off[k] : nullptr;
+        d.parent = tape ? b->d_tape + tape_off[k] + graphs[gof(k)]->n : nullptr;
+    }
+    std::vector<uint32_t> gen1(teams, 1u);
+    e = cudaMemcpyAsync(b->d_graphs, hg.data(), sizeof(BGraphDev) * n_graphs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_inst, hi.data(), sizeof(BInstDev) * n_inst, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_gen, gen1.data(), sizeof(uint32_t) * teams, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_m_of, b->m_of.data(), sizeof(uint32_t) * n_graphs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_stats, 0, sizeof(long long) * kBStats * n_inst, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.nstamp, 0, 4 * cap * teams, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.sstamp, 0, 4 * cap * teams, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.fflag, 0, 4 * cap * teams, st);
+    if (tape) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->d_grad64_ptr, hg64.data(), sizeof(double *) * n_graphs, cudaMemcpyHostToDevice, st);
+        for (int32_t i = 0; i < n_graphs && e == cudaSuccess; ++i) {
+            if (graphs[i]->m == 0) continue;
+            k_tail<<<std::max(1, std::min<int>(4096, (int)((graphs[i]->n + 15) / 16))), 512, 0, st>>>(
+                hg[i].vinfo, hg[i].n, (uint32_t *)hg[i].tail);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(cuda_status(e));
+    }
+    // the launch, as a CUDA graph: reset the queue, then the persistent kernel
+    BatchArgs &a = b->args;
+    a.graphs = b->d_graphs;
+    a.inst = b->d_inst;
+    a.n_inst = (uint32_t)n_inst;
+    a.queue = b->d_queue;
+    a.gen = b->d_gen;
+    a.err = b->d_err;
+    a.stats = b->d_stats;
+    a.ws = b->ws;
+    a.cap = cap;
+    a.max_phases = o.max_phases;
+    cudaGraphNode_t n_memset = nullptr, n_kernel = nullptr;
+    e = cudaGraphCreate(&b->graph, 0);
+    if (e == cudaSuccess) {
+        cudaMemsetParams mp{};
+        mp.dst = b->d_queue;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 1;
+        mp.height = 1;
+        mp.pitch = 4;
+        e = cudaGraphAddMemsetNode(&n_memset, b->graph, nullptr, 0, &mp);
+    }
+    if (e == cudaSuccess) {
+        void *kargs[] = {&b->args};
+        cudaKernelNodeParams kp{};
+        kp.func = dtype == DSSSP_F32 ? (tape ? (void *)k_batch<DSSSP_F32, true> : (void *)k_batch<DSSSP_F32, false>)
+                                     : (void *)k_batch<DSSSP_I32, false>;
+        kp.gridDim = dim3(b->teams);
+        kp.blockDim = dim3(kTeamThreads);
+        kp.sharedMemBytes = 0;
+        kp.kernelParams = kargs;
+        e = cudaGraphAddKernelNode(&n_kernel, b->graph, &n_memset, 1, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(cuda_status(e));
+    }
+    *out = b;
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream) {
+    if (!b) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    DSSSP_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    b->ran = true;
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_batch_sync(dsssp_batch *b, dsssp_batch_stats *stats, void *stream) {
+    if (!b) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    int err = 0;
+    std::vector<long long> hs;
+    DSSSP_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DSSSP_TRY(cudaMemsetAsync(b->d_err, 0, sizeof(int), st));
+    if (stats) {
+        hs.resize((size_t)kBStats * b->n_inst);
+        DSSSP_TRY(cudaMemcpyAsync(hs.data(), b->d_stats, sizeof(long long) * hs.size(), cudaMemcpyDeviceToHost, st));
+    }
+    DSSSP_TRY(cudaStreamSynchronize(st));
+    if (stats) {
+        for (int32_t k = 0; k < b->n_inst; ++k) {
+            const long long *x = hs.data() + (size_t)k * kBStats;
+            dsssp_batch_stats &o = stats[k];
+            std::memset(&o, 0, sizeof o);
+            o.buckets = x[BS_BUCKETS];
+            o.light_phases = x[BS_LIGHT];
+            o.heavy_phases = x[BS_HEAVY];
+            o.select_phases = x[BS_SELECT];
+            o.arcs_light = x[BS_ALIGHT];
+            o.arcs_heavy = x[BS_AHEAVY];
+            o.improvements = x[BS_IMPROVE];
+            o.far_scanned = x[BS_FARSCAN];
+            o.ns = x[BS_NS];
+            o.team = x[BS_TEAM];
+        }
+    }
+    return (dsssp_status)err;
+}
+
+dsssp_status dsssp_batch_destroy(dsssp_batch *b) {
+    if (!b) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    cudaDeviceSynchronize();
+    release(b);
+    return DSSSP_OK;
+}
+
+dsssp_status dsssp_solve_batched(dsssp_graph *const *graphs, int32_t n_graphs, const double *delta, int32_t n_inst,
+                                 const int32_t *src, const int32_t *src_graph, void *const *dist,
+                                 int32_t *const *pred, const dsssp_options *opt, dsssp_batch_stats *stats,
+                                 void *stream) {
+    dsssp_batch *b = nullptr;
+    dsssp_status rc = dsssp_batch_create(graphs, n_graphs, delta, n_inst, src, src_graph, dist, pred, 0u, opt,
+                                         stream, &b);
+    if (rc != DSSSP_OK) return rc;
+    rc = dsssp_batch_run(b, stream);
+    if (rc == DSSSP_OK) rc = dsssp_batch_sync(b, stats, stream);
+    dsssp_batch_destroy(b);
+    return rc;
+}
+
+dsssp_status dsssp_backward(dsssp_batch *b, const float *const *c, float *const *grad_w, uint32_t flags,
+                            void *stream) {
+    if (!b || !c || !grad_w || (flags & ~DSSSP_BACKWARD_ACCUMULATE)) return DSSSP_ERR_INVALID_ARG;
+    if (!b->tape || !b->ran) return DSSSP_ERR_NO_TAPE;
+    for (int32_t k = 0; k < b->n_inst; ++k)
+        if (!c[k]) return DSSSP_ERR_INVALID_ARG;
+    for (int32_t i = 0; i < b->n_graphs; ++i)
+        if (!grad_w[i] && b->m_of[i] > 0) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(b->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // pointer tables through pinned staging; the stream orders reuse of the staging buffer
+    DSSSP_TRY(cudaStreamSynchronize(st));
+    void **hp = (void **)b->h_ptrs;
+    for (int32_t i = 0; i < b->n_graphs; ++i) hp[i] = grad_w[i];
+    for (int32_t k = 0; k < b->n_inst; ++k) hp[b->n_graphs + k] = (void *)c[k];
+    DSSSP_TRY(cudaMemcpyAsync(b->d_gradw_ptr, hp, sizeof(void *) * b->n_graphs, cudaMemcpyHostToDevice, st));
+    DSSSP_TRY(cudaMemcpyAsync(b->d_c_ptr, hp + b->n_graphs, sizeof(void *) * b->n_inst, cudaMemcpyHostToDevice, st));
+    size_t sum_m = 0;
+    uint32_t max_m = 0;
+    for (uint32_t m : b->m_of) {
+        sum_m += m;
+        max_m = std::max(max_m, m);
+    }
+    if (sum_m) DSSSP_TRY(cudaMemsetAsync(b->d_grad64, 0, sizeof(double) * sum_m, st));
+    DSSSP_TRY(cudaMemsetAsync(b->d_queue + 1, 0, sizeof(uint32_t), st));
+    BwdArgs ba{};
+    ba.graphs = b->d_graphs;
+    ba.inst = b->d_inst;
+    ba.n_inst = (uint32_t)b->n_inst;
+    ba.queue = b->d_queue + 1;
+    ba.err = b->d_err;
+    ba.c = b->d_c_ptr;
+    ba.grad64 = b->d_grad64_ptr;
+    ba.ws = b->ws;
+    ba.cap = b->cap;
+    k_backward<<<b->teams, kTeamThreads, 0, st>>>(ba);
+    DSSSP_TRY(cudaGetLastError());
+    if (max_m) {
+        const dim3 grid((unsigned)std::min<uint32_t>(1024u, (max_m + 1023u) / 1024u), (unsigned)b->n_graphs);
+        k_grad_out<<<grid, 256, 0, st>>>(b->d_grad64_ptr, b->d_gradw_ptr, b->d_m_of,
+                                         (flags & DSSSP_BACKWARD_ACCUMULATE) ? 1 : 0);
+        DSSSP_TRY(cudaGetLastError());
+    }
+    return DSSSP_OK;
+}
+
+}  // extern "C"

@@ -35,6 +35,7 @@ DSSSP_ERR_NO_TAPE = 7
 DSSSP_ERR_OOM = 8
 DSSSP_ERR_UNSUPPORTED = 9
 DSSSP_ERR_TOO_LARGE = 10
+DSSSP_ERR_DEGENERATE = 11
 
 DSSSP_I32 = 0
 DSSSP_F32 = 1
@@ -43,6 +44,8 @@ DSSSP_MODE_STEPPED = 1
 DSSSP_FLAG_ASYNC = 0x1
 DSSSP_HOOK_NONE = 0
 DSSSP_HOOK_STALL_BARRIER = 1
+DSSSP_BATCH_TAPE = 0x1
+DSSSP_BACKWARD_ACCUMULATE = 0x1
 
 
 class dsssp_options(ctypes.Structure):
@@ -58,6 +61,15 @@ class dsssp_stats(ctypes.Structure):
         "vertices_heavy", "arcs_light", "arcs_heavy", "far_scanned", "improvements", "ns_light",
         "ns_heavy", "ns_rebin", "ns_total", "ns_first_arrival", "ns_arrival_spread", "grid_size",
         "block_size")] + [("reserved", ctypes.c_int64 * 6)]
+
+    def as_dict(self) -> dict:
+        return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class dsssp_batch_stats(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_int64) for name in (
+        "buckets", "light_phases", "heavy_phases", "select_phases", "arcs_light", "arcs_heavy",
+        "improvements", "far_scanned", "ns", "team")] + [("reserved", ctypes.c_int64 * 6)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
@@ -90,8 +102,21 @@ dsssp_graph_sync = _fn("dsssp_graph_sync", ctypes.c_int, [_vp, _vp])
 dsssp_solve_noalloc = _fn("dsssp_solve_noalloc", ctypes.c_int,
                           [_i64, _i64, _vp, _vp, _vp, ctypes.c_int, _i32, ctypes.c_double, _vp, _vp, _vp])
 
+_u32 = ctypes.c_uint32
+dsssp_batch_create = _fn("dsssp_batch_create", ctypes.c_int,
+                         [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, _u32, ctypes.POINTER(dsssp_options), _vp,
+                          ctypes.POINTER(_vp)])
+dsssp_batch_run = _fn("dsssp_batch_run", ctypes.c_int, [_vp, _vp])
+dsssp_batch_sync = _fn("dsssp_batch_sync", ctypes.c_int, [_vp, _vp, _vp])
+dsssp_batch_destroy = _fn("dsssp_batch_destroy", ctypes.c_int, [_vp])
+dsssp_solve_batched = _fn("dsssp_solve_batched", ctypes.c_int,
+                          [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(dsssp_options), _vp, _vp])
+dsssp_backward = _fn("dsssp_backward", ctypes.c_int, [_vp, _vp, _vp, _u32, _vp])
+
 EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create", "dsssp_graph_destroy",
-            "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc"]
+            "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc",
+            "dsssp_batch_create", "dsssp_batch_run", "dsssp_batch_sync", "dsssp_batch_destroy",
+            "dsssp_solve_batched", "dsssp_backward"]
 
 NOALLOC_MAX_VERTICES = 1 << 17
 
@@ -215,3 +240,112 @@ class Graph:
 
     def sync(self, stream=None) -> None:
         check(dsssp_graph_sync(self._h, _stream_ptr(stream)), "dsssp_graph_sync")
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))()
+    for i, p in enumerate(ptrs):
+        arr[i] = p
+    return arr
+
+
+class Batch:
+    """A batch plan: ``len(sources)`` solves run together in one persistent launch.
+
+    ``graphs`` is a Graph or a list of Graphs (one dtype, current device), ``deltas``
+    one Delta per graph, ``sources`` one source per instance and ``src_graph`` the
+    graph index of each instance (default: all on graph 0). Outputs are CUDA tensors
+    ``dist[k]`` (graph dtype) and ``pred[k]`` (int32), allocated unless given; every
+    ``run()`` rewrites them. ``tape=True`` records each instance's shortest-path tree
+    for ``backward()`` (float32 graphs only).
+    """
+
+    def __init__(self, graphs, deltas, sources, src_graph=None, dist=None, pred=None, tape: bool = False,
+                 options: dsssp_options | None = None, stream=None):
+        import torch
+        self._h = None
+        self.graphs = list(graphs) if isinstance(graphs, (list, tuple)) else [graphs]
+        deltas = list(deltas) if isinstance(deltas, (list, tuple, np.ndarray)) else [deltas]
+        if len(deltas) != len(self.graphs):
+            raise ValueError("one Delta per graph")
+        self.sources = [int(s) for s in sources]
+        k = len(self.sources)
+        self.src_graph = [0] * k if src_graph is None else [int(g) for g in src_graph]
+        if len(self.src_graph) != k:
+            raise ValueError("one graph index per source")
+        tdt = torch.float32 if self.graphs[0].dtype_code == DSSSP_F32 else torch.int32
+        ns = [self.graphs[g].n if 0 <= g < len(self.graphs) else 1 for g in self.src_graph]
+        self.dist = dist if dist is not None else [torch.empty(n, dtype=tdt, device="cuda") for n in ns]
+        self.pred = pred if pred is not None else [torch.empty(n, dtype=torch.int32, device="cuda") for n in ns]
+        if len(self.dist) != k or len(self.pred) != k:
+            raise ValueError("one dist and pred tensor per source")
+        for d, p, n in zip(self.dist, self.pred, ns):
+            if d.dtype != tdt or d.numel() < n or p.dtype != torch.int32 or p.numel() < n:
+                raise TypeError("dist/pred have the wrong dtype or size")
+        gh = _ptr_array([g.handle.value for g in self.graphs])
+        dl = (ctypes.c_double * len(deltas))(*[float(x) for x in deltas])
+        sr = (ctypes.c_int32 * k)(*self.sources)
+        sg = (ctypes.c_int32 * k)(*self.src_graph)
+        dp = _ptr_array([d.data_ptr() for d in self.dist])
+        pp = _ptr_array([p.data_ptr() for p in self.pred])
+        h = ctypes.c_void_p()
+        rc = dsssp_batch_create(gh, len(self.graphs), dl, k, sr, sg, dp, pp, DSSSP_BATCH_TAPE if tape else 0,
+                                ctypes.byref(options) if options is not None else None, _stream_ptr(stream),
+                                ctypes.byref(h))
+        check(rc, "dsssp_batch_create")
+        self._h = h
+        self.tape = tape
+
+    @property
+    def handle(self):
+        return self._h
+
+    def run(self, stream=None) -> None:
+        """Enqueue one run of every instance (one CUDA-graph launch); does not wait."""
+        check(dsssp_batch_run(self._h, _stream_ptr(stream)), "dsssp_batch_run")
+
+    def sync(self, stats: bool = False, stream=None):
+        """Wait; raise on a device-side error; optionally return per-instance counters."""
+        k = len(self.sources)
+        st = (dsssp_batch_stats * k)() if stats else None
+        check(dsssp_batch_sync(self._h, st, _stream_ptr(stream)), "dsssp_batch_sync")
+        return [x.as_dict() for x in st] if stats else None
+
+    def backward(self, c, grad_w, accumulate: bool = False, stream=None) -> None:
+        """grad_w[g] (float32[m_g], input arc order) = dL/dw for L = sum_k sum_v c[k][v] * dist[k][v]."""
+        import torch
+        if len(c) != len(self.sources) or len(grad_w) != len(self.graphs):
+            raise ValueError("one c per instance and one grad_w per graph")
+        for ck, g in zip(c, self.src_graph):
+            if ck.dtype != torch.float32 or not ck.is_cuda or ck.numel() < self.graphs[g].n:
+                raise TypeError("c[k] must be a CUDA float32 tensor of n entries")
+        for gw, g in zip(grad_w, self.graphs):
+            if gw.dtype != torch.float32 or not gw.is_cuda or gw.numel() < g.m:
+                raise TypeError("grad_w[g] must be a CUDA float32 tensor of m entries")
+        rc = dsssp_backward(self._h, _ptr_array([x.data_ptr() for x in c]),
+                            _ptr_array([x.data_ptr() for x in grad_w]),
+                            DSSSP_BACKWARD_ACCUMULATE if accumulate else 0, _stream_ptr(stream))
+        check(rc, "dsssp_backward")
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            dsssp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batched(graphs, deltas, sources, src_graph=None, options: dsssp_options | None = None,
+                  stats: bool = False, stream=None):
+    """One-shot batch: returns (dist list, pred list, stats list or None)."""
+    b = Batch(graphs, deltas, sources, src_graph=src_graph, options=options, stream=stream)
+    try:
+        b.run(stream)
+        st = b.sync(stats=stats, stream=stream)
+        return b.dist, b.pred, st
+    finally:
+        b.close()

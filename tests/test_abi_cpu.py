@@ -30,8 +30,8 @@ def test_library_exports_every_declared_entry_point():
 
 def test_status_strings_and_defaults():
     import paper_1911_06895_gb300 as ds
-    for s in range(10):
-        assert ds.dsssp_status_string(s)
+    for s in range(12):
+        assert ds.dsssp_status_string(s) != b"unknown status"
     assert ds.dsssp_status_string(999) == b"unknown status"
     o = ds.make_options()
     assert o.struct_size == ctypes.sizeof(ds.dsssp_options)
@@ -51,6 +51,17 @@ def test_null_arguments_rejected_without_gpu():
     assert ds.dsssp_graph_destroy(None) == ds.DSSSP_ERR_INVALID_ARG
     assert ds.dsssp_graph_sync(None, None) == ds.DSSSP_ERR_INVALID_ARG
     assert ds.dsssp_graph_info(None, None, None, None) == ds.DSSSP_ERR_INVALID_ARG
+    b = ctypes.c_void_p()
+    assert ds.dsssp_batch_create(None, 1, None, 1, None, None, None, None, 0, None, None,
+                                 ctypes.byref(b)) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_batch_create(None, 0, None, 0, None, None, None, None, 0, None, None,
+                                 None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_batch_run(None, None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_batch_sync(None, None, None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_batch_destroy(None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_backward(None, None, None, 0, None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_solve_batched(None, 1, None, 1, None, None, None, None, None, None,
+                                  None) == ds.DSSSP_ERR_INVALID_ARG
 
 
 def test_struct_layout_matches_header():
@@ -60,9 +71,10 @@ def test_struct_layout_matches_header():
     #include <stddef.h>
     #include "dsssp.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu\n", sizeof(dsssp_options), sizeof(dsssp_stats),
+      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dsssp_options), sizeof(dsssp_stats),
              offsetof(dsssp_options, max_phases), offsetof(dsssp_options, test_hook),
-             offsetof(dsssp_stats, block_size));
+             offsetof(dsssp_stats, block_size), sizeof(dsssp_batch_stats),
+             offsetof(dsssp_batch_stats, team));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -73,5 +85,6 @@ def test_struct_layout_matches_header():
         out = subprocess.check_output([exe]).decode().split()
     want = [ctypes.sizeof(ds.dsssp_options), ctypes.sizeof(ds.dsssp_stats),
             ds.dsssp_options.max_phases.offset, ds.dsssp_options.test_hook.offset,
-            ds.dsssp_stats.block_size.offset]
+            ds.dsssp_stats.block_size.offset, ctypes.sizeof(ds.dsssp_batch_stats),
+            ds.dsssp_batch_stats.team.offset]
     assert [int(x) for x in out] == want

@@ -1,0 +1,350 @@
+"""Batched solves and the adjoint through the C ABI, against the CPU oracle.
+
+Every instance of a batch must match the oracle's Dijkstra bit for bit
+(distances) and exactly (predecessors), like a single solve. Gradients are
+compared with the oracle's float64 subtree sums over the same tree (relative
+error <= 1e-5 per arc) and, independently, with central differences of the
+loss taken through the forward solve itself.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import graphgen
+import graphgen.workloads as W
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_06895_gb300 as ds
+    return ds
+
+
+def same(d, p, d_ref, p_ref, what=""):
+    if d.dtype == np.float32:
+        bad = np.flatnonzero(d.view(np.uint32) != d_ref.view(np.uint32))
+    else:
+        bad = np.flatnonzero(d != d_ref)
+    assert bad.size == 0, f"{what}: {bad.size} distances differ, first {bad[:5]} gpu {d[bad[:5]]} ref {d_ref[bad[:5]]}"
+    badp = np.flatnonzero(p != p_ref)
+    assert badp.size == 0, f"{what}: {badp.size} predecessors differ, first {badp[:5]}"
+
+
+def batch(ds, hs, deltas, sources, src_graph=None, tape=False, **opt):
+    o = ds.make_options(**opt) if opt else None
+    b = ds.Batch(hs, deltas, sources, src_graph=src_graph, tape=tape, options=o)
+    return b
+
+
+def fetch(b):
+    return [d.cpu().numpy() for d in b.dist], [p.cpu().numpy() for p in b.pred]
+
+
+# ------------------------------------------------------------------ forward
+
+@pytest.mark.parametrize("delta", [32.0, 1.0, math.inf])
+def test_many_sources_int(ds, delta):
+    g, srcs, _ = W.rmat14_int()
+    sources = srcs + [int(s) for s in graphgen.random_sources(g, 23, 11)]
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [delta], sources)
+    b.run()
+    st = b.sync(stats=True)
+    ds_, ps_ = fetch(b)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for k, s in enumerate(sources):
+        same(ds_[k], ps_[k], refd[k], refp[k], f"src {s} delta {delta}")
+        assert st[k]["buckets"] >= 1
+    b.close()
+    h.close()
+
+
+@pytest.mark.parametrize("delta", [0.01, 0.1, math.inf])
+def test_many_sources_fp32(ds, delta):
+    g, sources, _ = W.rmat22_unit(scale=16, n_sources=16)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [delta], sources)
+    b.run()
+    b.sync()
+    ds_, ps_ = fetch(b)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for k, s in enumerate(sources):
+        same(ds_[k], ps_[k], refd[k], refp[k], f"src {s} delta {delta}")
+
+
+def test_one_team_reuses_its_memory(ds):
+    """A single block solves every instance one after another, twice: stale stamps of
+    earlier instances and earlier launches must never be mistaken for current ones."""
+    g, sources, _ = W.rmat22_unit(scale=13, n_sources=12)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [0.05], sources, grid_size=1)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for rep in range(2):
+        for d in b.dist:
+            d.fill_(-1.0)
+        b.run()
+        st = b.sync(stats=True)
+        ds_, ps_ = fetch(b)
+        for k, s in enumerate(sources):
+            same(ds_[k], ps_[k], refd[k], refp[k], f"rep {rep} src {s}")
+            assert st[k]["team"] == 0
+    b.close()
+
+
+def edge_graphs():
+    out = []
+    out.append((graphgen.from_arcs(1, [], np.zeros(0, np.float32), dtype=np.float32), 0, 1.0))
+    out.append((graphgen.from_arcs(5, [(1, 2), (2, 3)], np.array([1, 1], np.float32), dtype=np.float32), 0, 1.0))
+    out.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (2, 1), (2, 3), (3, 0), (1, 1), (0, 1)],
+                                   np.array([0, 0, 0, 0.5, 0, 0.25, 0.0], np.float32), dtype=np.float32), 0, 0.3))
+    out.append((graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([3e38, 3e38], np.float32), dtype=np.float32),
+                0, 1e38))
+    k = 4000
+    rng = np.random.default_rng(3)
+    arcs = [(0, 1 + i) for i in range(k)] + [(1 + i, 0) for i in range(0, k, 7)] + [(5, 1 + i) for i in range(k)]
+    ws = np.concatenate([rng.random(k), np.zeros(len(range(0, k, 7))), rng.random(k) * 0.1]).astype(np.float32)
+    out.append((graphgen.from_arcs(k + 1, arcs, ws, dtype=np.float32), 0, 0.2))
+    n = 2000
+    wp = (np.random.default_rng(5).random(n - 1) * 10).astype(np.float32)
+    out.append((graphgen.from_arcs(n, [(i, i + 1) for i in range(n - 1)], wp, dtype=np.float32), 0, 0.7))
+    return out
+
+
+def test_many_graphs_uneven_sizes(ds):
+    """Graphs of very different sizes (ER family at small n, hand-built edge cases), a
+    Delta per graph, several instances on some graphs, one launch."""
+    graphs = [(g, s, d) for (g, s), d in zip(W.er_family(count=24, n_lo=50, n_hi=5000),
+                                               np.geomspace(0.02, 2.0, 24))]
+    graphs += edge_graphs()
+    hs = [ds.Graph(g.row_ptr, g.col, g.w) for g, _, _ in graphs]
+    sources, sg = [], []
+    for gi, (g, s, _) in enumerate(graphs):
+        sources.append(s)
+        sg.append(gi)
+    for gi in (0, 3, len(graphs) - 1):                   # more sources on a few graphs
+        g = graphs[gi][0]
+        for s in graphgen.random_sources(g, 3, 77 + gi):
+            sources.append(int(s))
+            sg.append(gi)
+    b = batch(ds, hs, [d for _, _, d in graphs], sources, src_graph=sg)
+    b.run()
+    b.sync()
+    ds_, ps_ = fetch(b)
+    for k, (s, gi) in enumerate(zip(sources, sg)):
+        g = graphs[gi][0]
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, s)
+        same(ds_[k], ps_[k], d_ref, p_ref, f"instance {k} graph {gi} src {s}")
+    b.close()
+
+
+def test_tape_forward_same_results(ds):
+    g, sources, _ = W.rmat22_unit(scale=14, n_sources=8)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for tape in (False, True):
+        b = batch(ds, h, [0.1], sources, tape=tape)
+        b.run()
+        b.sync()
+        ds_, ps_ = fetch(b)
+        for k, s in enumerate(sources):
+            same(ds_[k], ps_[k], refd[k], refp[k], f"tape {tape} src {s}")
+        b.close()
+
+
+def test_phase_cap_and_errors(ds):
+    g, sources, _ = W.rmat22_unit(scale=12, n_sources=4)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [0.01], sources, max_phases=3)
+    b.run()
+    with pytest.raises(ds.DsssError) as e:
+        b.sync()
+    assert e.value.status == ds.DSSSP_ERR_NOT_CONVERGED
+    b.run()                                              # the plan stays usable
+    with pytest.raises(ds.DsssError):
+        b.sync()
+    b.close()
+    with pytest.raises(ds.DsssError) as e:               # source out of range
+        ds.Batch(h, [0.1], [g.n])
+    assert e.value.status == ds.DSSSP_ERR_INVALID_ARG
+    b = batch(ds, h, [0.1], sources)                     # no tape: no backward
+    b.run()
+    b.sync()
+    c = [torch.ones(g.n, device="cuda") for _ in sources]
+    with pytest.raises(ds.DsssError) as e:
+        b.backward(c, [torch.zeros(g.m, device="cuda")])
+    assert e.value.status == ds.DSSSP_ERR_NO_TAPE
+    b.close()
+    gi = graphgen.from_arcs(3, [(0, 1)], np.array([1], np.int32), dtype=np.int32)
+    hi = ds.Graph(gi.row_ptr, gi.col, gi.w)
+    with pytest.raises(ds.DsssError) as e:               # a tape needs float32 weights
+        ds.Batch(hi, [1.0], [0], tape=True)
+    assert e.value.status == ds.DSSSP_ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ adjoint
+
+def gpu_grad(ds, b, cs, m):
+    gw = torch.empty(m, dtype=torch.float32, device="cuda")
+    b.backward([torch.from_numpy(c).cuda() for c in cs], [gw])
+    b.sync()
+    return gw.cpu().numpy().astype(np.float64)
+
+
+def assert_grad_close(g, ref, what=""):
+    err = np.abs(g - ref)
+    tol = 1e-5 * np.abs(ref) + 1e-30
+    bad = np.flatnonzero(err > tol)
+    assert bad.size == 0, f"{what}: {bad.size} arcs off, first {bad[:5]} gpu {g[bad[:5]]} ref {ref[bad[:5]]}"
+    assert np.linalg.norm(g - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("delta", [0.3, 2.0])
+def test_backward_matches_oracle_gradient(ds, delta):
+    g, sources, c0 = W.rmat20_lognormal(scale=14, n_sources=8)
+    cs = [graphgen.random_costs(g.n, 1000 + k) for k in range(len(sources))]
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [delta], sources, tape=True)
+    b.run()
+    b.sync()
+    ref = oracle.tree_gradient_many(g.row_ptr, g.col, g.w, sources, delta, cs)
+    gg = gpu_grad(ds, b, cs, g.m)
+    assert np.count_nonzero(ref) > 1000
+    assert_grad_close(gg, ref, f"delta {delta}")
+    # accumulate adds into the output
+    gw = torch.from_numpy(gg.astype(np.float32)).cuda()
+    b.backward([torch.from_numpy(c).cuda() for c in cs], [gw], accumulate=True)
+    b.sync()
+    np.testing.assert_allclose(gw.cpu().numpy(), 2 * gg.astype(np.float32), rtol=1e-6)
+    b.close()
+
+
+def test_backward_special_cases(ds):
+    # parallel arcs that both realise dist[2]: the light one is the tree arc
+    big = float(2 ** 24)
+    g = graphgen.from_arcs(3, [(0, 1), (1, 2), (1, 2)], np.array([big, 1.0, 0.25], np.float32), dtype=np.float32)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [0.5], [0], tape=True)
+    b.run()
+    b.sync()
+    c = [np.array([0, 1, 1], np.float32)]
+    np.testing.assert_array_equal(gpu_grad(ds, b, c, g.m), oracle.tree_gradient(g.row_ptr, g.col, g.w, 0, 0.5, c[0]))
+    b.close()
+    # a zero-weight cycle in the predecessor graph: no gradient
+    g = graphgen.from_arcs(4, [(0, 3), (3, 1), (3, 2), (1, 2), (2, 1)], np.array([1, 0, 0, 0, 0], np.float32),
+                           dtype=np.float32)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [1.0], [0], tape=True)
+    b.run()
+    b.sync()
+    b.backward([torch.ones(4, device="cuda")], [torch.zeros(g.m, device="cuda")])
+    with pytest.raises(ds.DsssError) as e:
+        b.sync()
+    assert e.value.status == ds.DSSSP_ERR_DEGENERATE
+    b.close()
+
+
+def test_autograd_and_central_differences(ds):
+    """torch.autograd through the library, then central differences of the loss taken
+    through the forward solve itself (float32 distances, eps = 1e-3)."""
+    from paper_1911_06895_gb300.autograd import shortest_path_distances
+    g, sources, _ = W.rmat20_lognormal(scale=11, n_sources=4)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    cl = torch.from_numpy(g.col).cuda()
+    w = torch.from_numpy(g.w).cuda().requires_grad_(True)
+    c = torch.from_numpy(np.stack([graphgen.random_costs(g.n, 5 + k) for k in range(len(sources))])).cuda()
+    delta = 1.0
+    dist, pred = shortest_path_distances(w, rp, cl, sources, delta)
+    ok = torch.isfinite(dist)
+    loss = (c * torch.where(ok, dist, torch.zeros_like(dist))).double().sum()
+    loss.backward()
+    grad = w.grad.cpu().numpy().astype(np.float64)
+    ref = oracle.tree_gradient_many(g.row_ptr, g.col, g.w, sources, delta, [x for x in c.cpu().numpy()])
+    assert_grad_close(grad, ref, "autograd")
+
+    def loss_at(wv):
+        with torch.no_grad():
+            d, p = shortest_path_distances(wv, rp, cl, sources, delta)
+            okk = torch.isfinite(d)
+            return float((c.double() * torch.where(okk, d, torch.zeros_like(d)).double()).sum()), p
+
+    base_pred = pred.clone()
+    rng = np.random.default_rng(0)
+    arcs = rng.choice(g.m, 150, replace=False)
+    checked = 0
+    for e in arcs:
+        w0 = float(g.w[e])
+        wp, wm = w.detach().clone(), w.detach().clone()
+        wp[e] = w0 + 1e-3
+        wm[e] = max(w0 - 1e-3, 0.0)
+        hp = float(wp[e]) - w0
+        hm = w0 - float(wm[e])
+        lp, pp = loss_at(wp)
+        lm, pm = loss_at(wm)
+        if not (torch.equal(pp, base_pred) and torch.equal(pm, base_pred)):
+            continue                                        # the tree changes within eps: a kink
+        fd = (lp - lm) / (hp + hm)
+        assert abs(fd - grad[e]) <= 2e-2 * abs(grad[e]) + 2e-3, (e, fd, grad[e])
+        checked += 1
+    assert checked >= 100
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+def test_full_rmat20_256_sources(ds):
+    """R-MAT scale 20, fp32 U[0,1), 256 sources in one launch: 8 instances exact, all by invariants."""
+    g, sources = W.rmat20_unit()
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [0.1], sources)
+    b.run()
+    b.sync()
+    ds_, ps_ = fetch(b)
+    pick = list(range(0, 256, 32))
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, [sources[k] for k in pick])
+    for j, k in enumerate(pick):
+        same(ds_[k], ps_[k], refd[j], refp[j], f"src {sources[k]}")
+    for k in range(0, 256, 5):
+        assert oracle.check_invariants(g.row_ptr, g.col, g.w, sources[k], ds_[k], ps_[k]) == 0
+    b.close()
+
+
+def test_full_er_family_512(ds):
+    """512 ER graphs, n log-uniform in [1e3, 2e5], one source each, one launch: all exact."""
+    fam = W.er_family()
+    hs = [ds.Graph(g.row_ptr, g.col, g.w) for g, _ in fam]
+    b = batch(ds, hs, [0.1] * len(fam), [s for _, s in fam], src_graph=list(range(len(fam))))
+    b.run()
+    b.sync()
+    ds_, ps_ = fetch(b)
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor() as ex:
+        refs = list(ex.map(lambda gs: oracle.dijkstra(gs[0].row_ptr, gs[0].col, gs[0].w, gs[1]), fam))
+    for k, ((g, s), (d_ref, p_ref)) in enumerate(zip(fam, refs)):
+        same(ds_[k], ps_[k], d_ref, p_ref, f"graph {k} ({g.name})")
+    b.close()
+
+
+def test_full_rmat20_lognormal_gradient(ds):
+    """R-MAT scale 20, lognormal(0, 1) weights, 32 sources, c ~ U[0,1): forward exact on two
+    sources, gradient within 1e-5 (relative, per arc) of the oracle's float64 subtree sums."""
+    g, sources, c = W.rmat20_lognormal()
+    delta = 1.0
+    cs = [c] * len(sources)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [delta], sources, tape=True)
+    b.run()
+    b.sync()
+    ds_, ps_ = fetch(b)
+    for k in (0, 31):
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, sources[k])
+        same(ds_[k], ps_[k], d_ref, p_ref, f"src {sources[k]}")
+    gg = gpu_grad(ds, b, cs, g.m)
+    ref = oracle.tree_gradient_many(g.row_ptr, g.col, g.w, sources, delta, cs)
+    assert_grad_close(gg, ref, "scale 20")
+    b.close()
