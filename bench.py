@@ -17,6 +17,10 @@ roofline  the solve kernel's algorithmic bytes (per-unit figures below) over
         its CUDA-event time, against the measured HBM copy bandwidth.
 cpu_baseline  the CPU oracle (binary-heap Dijkstra, one source per host core)
         on a bounded sample of the same sources.
+batched / fwd_bwd  (one GPU) batched solves and the forward + adjoint pass against
+        the plain per-source solve on the same GPU: 256 sources on a scale-20 R-MAT,
+        512 ER graphs of uneven sizes, 32 sources on a scale-20 lognormal R-MAT with
+        dLoss/dw; Delta chosen by the autotuner.
 
 Multi-GPU (torchrun): every rank solves its own 64 sources on its own copy of
 the graph (weak scaling, no collective on the data path); value sums the
@@ -217,6 +221,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-sources", type=int, default=0, help="CPU baseline sample (0: one per core)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and forward+backward comparisons")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling driver: run this many solves at --profile-delta and exit (for ncu)")
     ap.add_argument("--profile-delta", default="0.1",
@@ -332,6 +338,10 @@ def main():
     if not args.no_e2e:
         e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args)
 
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras = run_extras(ds, torch)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
@@ -362,10 +372,123 @@ def main():
             "clocks": clk,
             "gpu_launches": 4 * solves * args.steps,
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist_pg:
         dist_pg.barrier()
         dist_pg.destroy_process_group()
+
+
+def _events_ms(torch, fn, reps: int, stream=None) -> float:
+    """Median CUDA-event time of fn() over reps runs after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_extras(ds, torch):
+    """Batched and forward+backward throughput against the plain per-source solve on the
+    same GPU: (a) 256 sources on a scale-20 R-MAT in one launch, (b) 512 ER graphs of
+    uneven sizes in one launch, (c) 32 sources on a scale-20 lognormal R-MAT with the
+    adjoint. Delta is chosen by the autotuner (batch instances for the batch, single
+    solves for the plain runs); tuning time is reported, not timed."""
+    import graphgen.workloads as W
+    out = {"batched": {}, "fwd_bwd": {}}
+    o_async = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
+
+    # (a) many sources on one graph
+    g, srcs = W.rmat20_unit()
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    t = time.perf_counter()
+    (d_b,), _ = ds.autotune(h, [srcs[:8]], target="batch")
+    (d_p,), _ = ds.autotune(h, [srcs[:4]], target="solve")
+    tune_s = time.perf_counter() - t
+    b = ds.Batch(h, [d_b], srcs)
+    ms_b = _events_ms(torch, b.run, 3)
+    b.sync()
+    b.close()
+
+    def plain_a():
+        for s in srcs:
+            h.solve(s, d_p, options=o_async)
+    ms_p = _events_ms(torch, plain_a, 1)
+    h.sync()
+    h.close()
+    out["batched"]["rmat20_unit_256src"] = {
+        "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "ms": ms_b,
+        "gteps": g.m * len(srcs) / (ms_b * 1e-3) / 1e9, "plain_delta": d_p, "plain_ms": ms_p,
+        "plain_gteps": g.m * len(srcs) / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s}
+
+    # (b) many graphs of uneven sizes
+    fam = W.er_family()
+    hs = [ds.Graph(x.row_ptr, x.col, x.w) for x, _ in fam]
+    fsrc = [s for _, s in fam]
+    msum = sum(x.m for x, _ in fam)
+    t = time.perf_counter()
+    deltas, _ = ds.autotune(hs, [[s] for s in fsrc], target="batch", refine=1)
+    tune_s = time.perf_counter() - t
+    b = ds.Batch(hs, deltas, fsrc, src_graph=list(range(len(fam))))
+    ms_b = _events_ms(torch, b.run, 3)
+    b.sync()
+    b.close()
+    for hh, d in zip(hs, deltas):
+        hh.prepare(d)
+
+    def plain_b():
+        for hh, s, d in zip(hs, fsrc, deltas):
+            hh.solve(s, d, options=o_async)
+    ms_p = _events_ms(torch, plain_b, 1)
+    for hh in hs:
+        hh.sync()
+        hh.close()
+    out["batched"]["er512"] = {
+        "graphs": len(fam), "sum_n": sum(x.n for x, _ in fam), "sum_m": msum,
+        "delta_range": [min(deltas), max(deltas)], "ms": ms_b, "gteps": msum / (ms_b * 1e-3) / 1e9,
+        "plain_ms": ms_p, "plain_gteps": msum / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s}
+
+    # (c) forward + backward
+    g, srcs, c = W.rmat20_lognormal()
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    t = time.perf_counter()
+    (d_b,), _ = ds.autotune(h, [srcs[:8]], target="batch")
+    tune_s = time.perf_counter() - t
+    cs = [torch.from_numpy(c).cuda()] * len(srcs)
+    gw = torch.empty(g.m, dtype=torch.float32, device="cuda")
+    bt = ds.Batch(h, [d_b], srcs, tape=True)
+    bn = ds.Batch(h, [d_b], srcs)
+
+    def fwd_bwd():
+        bt.run()
+        bt.backward(cs, [gw])
+    ms_fb = _events_ms(torch, fwd_bwd, 3)
+    ms_f = _events_ms(torch, bn.run, 3)
+    ms_bw = _events_ms(torch, lambda: bt.backward(cs, [gw]), 3)
+    bt.sync()
+    bn.sync()
+    bt.close()
+    bn.close()
+
+    def plain_c():
+        for s in srcs:
+            h.solve(s, d_b, options=o_async)
+    ms_p = _events_ms(torch, plain_c, 1)
+    h.sync()
+    h.close()
+    sm = g.m * len(srcs)
+    out["fwd_bwd"]["rmat20_lognormal_32src"] = {
+        "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "fwd_bwd_ms": ms_fb, "fwd_ms": ms_f,
+        "bwd_ms": ms_bw, "fwd_bwd_gteps": sm / (ms_fb * 1e-3) / 1e9, "fwd_gteps": sm / (ms_f * 1e-3) / 1e9,
+        "plain_solve_ms": ms_p, "plain_solve_gteps": sm / (ms_p * 1e-3) / 1e9,
+        "fwd_bwd_over_fwd": ms_fb / ms_f, "tune_s": tune_s}
+    return out
 
 
 def profile_driver(args):

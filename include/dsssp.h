@@ -298,6 +298,39 @@ dsssp_status dsssp_solve_batched(dsssp_graph *const *graphs, int32_t n_graphs, c
 dsssp_status dsssp_backward(dsssp_batch *b, const float *const *c, float *const *grad_w, uint32_t flags,
                             void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Autotuning of Delta. The paper fixes Delta by hand (Section VI-A uses      */
+/* Delta = 1 on unit weights); delta-stepping's work and phase count trade    */
+/* off through Delta (Section III: small Delta approaches Dijkstra's order,  */
+/* large Delta Bellman-Ford's). The tuner times sample solves on this GPU    */
+/* and returns, per graph, the Delta with the least device time.             */
+
+/* dsssp_tune_options.target */
+#define DSSSP_TUNE_SOLVE 0   /* time dsssp_solve, one sample source after another                 */
+#define DSSSP_TUNE_BATCH 1   /* time instances of a batch (each on one block, as dsssp_batch_run)  */
+
+typedef struct {
+    uint32_t struct_size;    /* sizeof(dsssp_tune_options)                                        */
+    int32_t  target;         /* DSSSP_TUNE_SOLVE or DSSSP_TUNE_BATCH                              */
+    int32_t  n_candidates;   /* 0: a ladder of 7 powers of two around mean weight / mean degree x 4  */
+    int32_t  refine;         /* refinement rounds (each tries the best x 2^(+-1/2^r)); default 2, -1: none */
+    double   candidates[16]; /* explicit candidates (> 0) when n_candidates > 0                   */
+    int32_t  reserved[8];
+} dsssp_tune_options;
+
+/* Choose Delta for every graph:
+ *   graphs       HOST array of n_graphs handles (one dtype, current device);
+ *   sample_src   HOST array of n_graphs * k sample sources (k per graph, graph-major);
+ *   opt          NULL for defaults (DSSSP_TUNE_SOLVE, default ladder, 2 refinement rounds);
+ *   delta_out    HOST array of n_graphs: the chosen Delta;
+ *   ms_out       NULL or HOST array of n_graphs: device time of the k samples at that Delta.
+ * With DSSSP_TUNE_BATCH every (graph, candidate, source) is one instance of a tuning batch
+ * and its cost is that instance's device time. The light/heavy splits the tuner builds stay
+ * cached in the handles. Waits for its work. Errors: INVALID_ARG, OOM, CUDA and those of
+ * dsssp_solve / dsssp_batch_create. */
+dsssp_status dsssp_autotune(dsssp_graph *const *graphs, int32_t n_graphs, const int32_t *sample_src, int32_t k,
+                            const dsssp_tune_options *opt, double *delta_out, double *ms_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

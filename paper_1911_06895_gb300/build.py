@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdsssp.so")
-SOURCES = ["api.cu", "split.cu", "solve.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "split.cu", "solve.cu", "noalloc.cu", "batch.cu", "tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 

@@ -46,6 +46,8 @@ DSSSP_HOOK_NONE = 0
 DSSSP_HOOK_STALL_BARRIER = 1
 DSSSP_BATCH_TAPE = 0x1
 DSSSP_BACKWARD_ACCUMULATE = 0x1
+DSSSP_TUNE_SOLVE = 0
+DSSSP_TUNE_BATCH = 1
 
 
 class dsssp_options(ctypes.Structure):
@@ -73,6 +75,11 @@ class dsssp_batch_stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
+
+
+class dsssp_tune_options(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_uint32), ("target", ctypes.c_int32), ("n_candidates", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("candidates", ctypes.c_double * 16), ("reserved", ctypes.c_int32 * 8)]
 
 
 _vp = ctypes.c_void_p
@@ -112,11 +119,13 @@ dsssp_batch_destroy = _fn("dsssp_batch_destroy", ctypes.c_int, [_vp])
 dsssp_solve_batched = _fn("dsssp_solve_batched", ctypes.c_int,
                           [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(dsssp_options), _vp, _vp])
 dsssp_backward = _fn("dsssp_backward", ctypes.c_int, [_vp, _vp, _vp, _u32, _vp])
+dsssp_autotune = _fn("dsssp_autotune", ctypes.c_int,
+                     [_vp, _i32, _vp, _i32, ctypes.POINTER(dsssp_tune_options), _vp, _vp, _vp])
 
 EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create", "dsssp_graph_destroy",
             "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc",
             "dsssp_batch_create", "dsssp_batch_run", "dsssp_batch_sync", "dsssp_batch_destroy",
-            "dsssp_solve_batched", "dsssp_backward"]
+            "dsssp_solve_batched", "dsssp_backward", "dsssp_autotune"]
 
 NOALLOC_MAX_VERTICES = 1 << 17
 
@@ -349,3 +358,32 @@ def solve_batched(graphs, deltas, sources, src_graph=None, options: dsssp_option
         return b.dist, b.pred, st
     finally:
         b.close()
+
+
+def autotune(graphs, sample_sources, target: str = "solve", candidates=None, refine: int = 2, stream=None):
+    """Choose Delta per graph by timing sample solves on this GPU.
+
+    ``sample_sources`` is one list of k sources per graph (or one list for a single
+    graph); ``target`` is "solve" (dsssp_solve) or "batch" (instances of a batch).
+    Returns (deltas, ms): the chosen Delta of each graph and the device time of its
+    k samples at that Delta."""
+    graphs = list(graphs) if isinstance(graphs, (list, tuple)) else [graphs]
+    if graphs and not isinstance(sample_sources[0], (list, tuple, np.ndarray)):
+        sample_sources = [sample_sources]
+    k = len(sample_sources[0])
+    if len(sample_sources) != len(graphs) or any(len(s) != k for s in sample_sources):
+        raise ValueError("k sample sources per graph")
+    o = dsssp_tune_options()
+    o.struct_size = ctypes.sizeof(dsssp_tune_options)
+    o.target = DSSSP_TUNE_BATCH if target == "batch" else DSSSP_TUNE_SOLVE
+    o.refine = refine if refine != 0 else -1
+    if candidates:
+        o.n_candidates = len(candidates)
+        for i, c in enumerate(candidates):
+            o.candidates[i] = float(c)
+    flat = (ctypes.c_int32 * (len(graphs) * k))(*[int(s) for ss in sample_sources for s in ss])
+    dout = (ctypes.c_double * len(graphs))()
+    mout = (ctypes.c_double * len(graphs))()
+    check(dsssp_autotune(_ptr_array([g.handle.value for g in graphs]), len(graphs), flat, k, ctypes.byref(o),
+                         dout, mout, _stream_ptr(stream)), "dsssp_autotune")
+    return list(dout), list(mout)

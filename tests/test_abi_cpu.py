@@ -22,7 +22,7 @@ def test_library_exports_every_declared_entry_point():
     import paper_1911_06895_gb300 as ds
     lib = ctypes.CDLL(ds.LIB_PATH)
     names = declared_functions()
-    assert len(names) >= 8
+    assert len(names) >= 16
     for name in names:
         assert hasattr(lib, name), name
     assert set(names) == set(ds.EXPORTED)
@@ -62,6 +62,7 @@ def test_null_arguments_rejected_without_gpu():
     assert ds.dsssp_backward(None, None, None, 0, None) == ds.DSSSP_ERR_INVALID_ARG
     assert ds.dsssp_solve_batched(None, 1, None, 1, None, None, None, None, None, None,
                                   None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_autotune(None, 1, None, 1, None, None, None, None) == ds.DSSSP_ERR_INVALID_ARG
 
 
 def test_struct_layout_matches_header():
@@ -75,6 +76,7 @@ def test_struct_layout_matches_header():
              offsetof(dsssp_options, max_phases), offsetof(dsssp_options, test_hook),
              offsetof(dsssp_stats, block_size), sizeof(dsssp_batch_stats),
              offsetof(dsssp_batch_stats, team));
+      printf("%zu %zu\n", sizeof(dsssp_tune_options), offsetof(dsssp_tune_options, candidates));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -86,5 +88,6 @@ def test_struct_layout_matches_header():
     want = [ctypes.sizeof(ds.dsssp_options), ctypes.sizeof(ds.dsssp_stats),
             ds.dsssp_options.max_phases.offset, ds.dsssp_options.test_hook.offset,
             ds.dsssp_stats.block_size.offset, ctypes.sizeof(ds.dsssp_batch_stats),
-            ds.dsssp_batch_stats.team.offset]
+            ds.dsssp_batch_stats.team.offset, ctypes.sizeof(ds.dsssp_tune_options),
+            ds.dsssp_tune_options.candidates.offset]
     assert [int(x) for x in out] == want

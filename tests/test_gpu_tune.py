@@ -1,0 +1,70 @@
+"""The Delta autotuner: it returns a Delta from the candidates it tried, and
+distances at the chosen Delta stay exact (Delta only orders the work)."""
+import numpy as np
+import pytest
+
+import graphgen
+import graphgen.workloads as W
+import oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ds():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_06895_gb300 as ds
+    return ds
+
+
+def test_tune_single_solve_explicit_candidates(ds):
+    g, srcs, _ = W.rmat14_int()
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    cands = [4.0, 16.0, 64.0, 256.0]
+    sample = [int(s) for s in graphgen.random_sources(g, 3, 5)]
+    (d,), (ms,) = ds.autotune(h, sample, target="solve", candidates=cands, refine=-1)
+    assert d in cands and ms > 0
+    r = h.solve(srcs[0], d)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, srcs[0])
+    assert np.array_equal(r.dist.cpu().numpy(), d_ref) and np.array_equal(r.pred.cpu().numpy(), p_ref)
+
+
+def test_tune_default_ladder_with_refinement(ds):
+    g, srcs, _ = W.rmat22_unit(scale=14, n_sources=4)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    (d,), (ms,) = ds.autotune(h, srcs[:2], target="solve")
+    mean_w = float(np.mean(g.w, dtype=np.float64))
+    d0 = 4 * mean_w / (g.m / g.n)
+    ratio = np.log2(d / d0)
+    assert -3.75 <= ratio <= 3.75                    # within the ladder plus refinement steps
+    assert abs(ratio * 4 - round(ratio * 4)) < 1e-9  # a quarter-power-of-two step from the start
+    r = h.solve(srcs[2], d)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, srcs[2])
+    assert np.array_equal(r.dist.cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
+
+
+def test_tune_batch_per_graph(ds):
+    fam = W.er_family(count=12, n_lo=500, n_hi=20000)
+    hs = [ds.Graph(g.row_ptr, g.col, g.w) for g, _ in fam]
+    sample = [[s] + [int(x) for x in graphgen.random_sources(g, 1, 9)] for g, s in fam]
+    deltas, ms = ds.autotune(hs, sample, target="batch")
+    assert len(deltas) == len(fam) and all(d > 0 for d in deltas) and all(t > 0 for t in ms)
+    b = ds.Batch(hs, deltas, [s for _, s in fam], src_graph=list(range(len(fam))))
+    b.run()
+    b.sync()
+    for k, (g, s) in enumerate(fam):
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, s)
+        assert np.array_equal(b.dist[k].cpu().numpy().view(np.uint32), d_ref.view(np.uint32)), k
+        assert np.array_equal(b.pred[k].cpu().numpy(), p_ref), k
+    b.close()
+
+
+def test_tune_rejects_bad_arguments(ds):
+    g, srcs, _ = W.rmat14_int(scale=10)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    with pytest.raises(ds.DsssError):
+        ds.autotune(h, [g.n], target="solve")
+    with pytest.raises(ds.DsssError):
+        ds.autotune(h, srcs, target="solve", candidates=[-1.0])
