@@ -29,6 +29,8 @@
 // DSSSP_ERR_TIMEOUT instead of hanging. Phases with little work run on block 0
 // alone (solo). DSSSP_MODE_STEPPED launches one kernel per phase and runs the
 // serial step as a 1-thread kernel.
+#include <mutex>
+
 #include "dsssp_internal.cuh"
 
 namespace dsssp {
@@ -89,22 +91,34 @@ struct BlockView {
 };
 
 // ---------------------------------------------------------------------------
-// Per-warp staging of pushes in shared memory: a list counter is touched once
-// per 32 staged entries, not once per 32-arc step, and list stores are wide.
+// Per-warp staging of pushes in shared memory: a list counter (shared by the
+// whole grid) is touched once per kFlush staged entries, not once per 32-arc
+// step. A staging call adds at most 32 entries, so kFlush + 32 slots suffice.
+constexpr uint32_t kFlush = 64;
+constexpr uint32_t kStage = kFlush + 32;
+// Improved vertices wait in a per-warp record buffer and are classified 32 at a
+// time, so the stamp exchanges of a whole batch are in flight together instead
+// of one dependent round trip per 32-arc step.
+constexpr uint32_t kRec = 32 + 32 * kIlp;
+
 struct WarpStage {
-    uint32_t fv[64], fd[64];             // next frontier (vertex, light degree)
-    uint32_t sv[64], sd[64];             // S (vertex, heavy degree)
-    uint32_t bt[64], bv[64], bd[64];     // bucket slots (slot, vertex, light degree; 0: heavy-only list)
-    uint32_t ov[64];                     // overflow
+    uint32_t fv[kStage], fd[kStage];             // next frontier (vertex, light degree)
+    uint32_t sv[kStage], sd[kStage];             // S (vertex, heavy degree)
+    uint32_t bt[kStage], bv[kStage], bd[kStage]; // bucket slots (slot, vertex, light degree; 0: heavy-only list)
+    uint32_t ov[kStage];                         // overflow
+    uint32_t iv[kRec], ik[kRec];                 // improvement records (vertex, new key)
 };
 
-// Append n <= 32 staged (vertex, degree) entries (lanes < n) to an arc list.
+// Append n <= 64 staged (vertex, degree) entries to an arc list; lane l holds
+// entries 2l and 2l+1.
 __device__ __forceinline__ void flush_arc_entries(const uint32_t *bv, const uint32_t *bd, uint32_t n, uint2 *list,
                                                   unsigned long long *ctr) {
     const uint32_t lane = lane_id();
-    const bool has = lane < n;
-    const uint32_t v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u;
-    uint32_t incl = d;
+    const uint32_t j = 2u * lane;
+    const bool h0 = j < n, h1 = j + 1u < n;
+    const uint32_t v0 = h0 ? bv[j] : 0u, d0 = h0 ? bd[j] : 0u;
+    const uint32_t v1 = h1 ? bv[j + 1u] : 0u, d1 = h1 ? bd[j + 1u] : 0u;
+    uint32_t incl = d0 + d1;
     #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const uint32_t t = __shfl_up_sync(FULL, incl, o);
@@ -114,7 +128,9 @@ __device__ __forceinline__ void flush_arc_entries(const uint32_t *bv, const uint
     unsigned long long old = 0;
     if (lane == 0) old = atomicAdd(ctr, ((unsigned long long)n << 32) | tot);
     old = __shfl_sync(FULL, old, 0);
-    if (has) list[(uint32_t)(old >> 32) + lane] = make_uint2(v, (uint32_t)old + incl - d);
+    const uint32_t base = (uint32_t)(old >> 32) + j, off = (uint32_t)old + incl - d0 - d1;
+    if (h0) list[base] = make_uint2(v0, off);
+    if (h1) list[base + 1u] = make_uint2(v1, off + d0);
 }
 
 __device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32_t *list, uint32_t *counter) {
@@ -123,12 +139,13 @@ __device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32
     if (lane == 0) base = atomicAdd(counter, n);
     base = __shfl_sync(FULL, base, 0);
     if (lane < n) list[base + lane] = bv[lane];
+    if (lane + 32u < n) list[base + lane + 32u] = bv[lane + 32u];
 }
 
 // Append n <= 32 staged slot entries: lanes are grouped by (slot, list) and
 // each group takes one atomic on its slot's counter.
-__device__ __forceinline__ void flush_slot_entries(const SolveArgs &a, const uint32_t *bt, const uint32_t *bv,
-                                                   const uint32_t *bd, uint32_t n) {
+__device__ __forceinline__ void flush_slot_entries32(const SolveArgs &a, const uint32_t *bt, const uint32_t *bv,
+                                                     const uint32_t *bd, uint32_t n) {
     const uint32_t lane = lane_id();
     const bool has = lane < n;
     const uint32_t t = has ? bt[lane] : 0u, v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u;
@@ -165,6 +182,12 @@ __device__ __forceinline__ void flush_slot_entries(const SolveArgs &a, const uin
     }
 }
 
+__device__ __forceinline__ void flush_slot_entries(const SolveArgs &a, const uint32_t *bt, const uint32_t *bv,
+                                                   const uint32_t *bd, uint32_t n) {
+    flush_slot_entries32(a, bt, bv, bd, min(n, 32u));
+    if (n > 32u) flush_slot_entries32(a, bt + 32, bv + 32, bd + 32, n - 32u);
+}
+
 // ---------------------------------------------------------------------------
 // Block-local accumulators flushed to the control block.
 struct BlockAcc {
@@ -196,7 +219,8 @@ __device__ __forceinline__ uint32_t ov_index(const PhaseDesc &d) {
     return d.mode == MODE_REBIN ? d.ov_cur ^ 1u : d.ov_cur;
 }
 
-// Stage one entry per pushing lane of `kind`; flush 32 when the buffer is full.
+// Stage one entry per pushing lane; flush kFlush entries when the buffer holds
+// that many, keeping the rest (fewer than 32) at its front.
 __device__ __forceinline__ void stage_arc_entry(bool pred, uint32_t v, uint32_t deg, uint32_t *bv, uint32_t *bd,
                                                 uint32_t &cnt, uint2 *list, unsigned long long *ctr) {
     const uint32_t mask = __ballot_sync(FULL, pred);
@@ -204,15 +228,16 @@ __device__ __forceinline__ void stage_arc_entry(bool pred, uint32_t v, uint32_t 
     const uint32_t lane = lane_id();
     if (pred) {
         const uint32_t k = cnt + __popc(mask & lanemask_lt());
-        bv[k] = v; bd[k] = deg;
+        bv[k] = v;
+        bd[k] = deg;
     }
     cnt += __popc(mask);
     __syncwarp();
-    if (cnt >= 32u) {
-        flush_arc_entries(bv, bd, 32u, list, ctr);
-        const uint32_t rest = cnt - 32u;
+    if (cnt >= kFlush) {
+        flush_arc_entries(bv, bd, kFlush, list, ctr);
+        const uint32_t rest = cnt - kFlush;
         uint32_t x = 0, y = 0;
-        if (lane < rest) { x = bv[32 + lane]; y = bd[32 + lane]; }
+        if (lane < rest) { x = bv[kFlush + lane]; y = bd[kFlush + lane]; }
         __syncwarp();
         if (lane < rest) { bv[lane] = x; bd[lane] = y; }
         __syncwarp();
@@ -231,11 +256,11 @@ __device__ __forceinline__ void stage_slot_entry(const SolveArgs &a, bool pred, 
     }
     cnt += __popc(mask);
     __syncwarp();
-    if (cnt >= 32u) {
-        flush_slot_entries(a, ws.bt, ws.bv, ws.bd, 32u);
-        const uint32_t rest = cnt - 32u;
+    if (cnt >= kFlush) {
+        flush_slot_entries(a, ws.bt, ws.bv, ws.bd, kFlush);
+        const uint32_t rest = cnt - kFlush;
         uint32_t x = 0, y = 0, z = 0;
-        if (lane < rest) { x = ws.bt[32 + lane]; y = ws.bv[32 + lane]; z = ws.bd[32 + lane]; }
+        if (lane < rest) { x = ws.bt[kFlush + lane]; y = ws.bv[kFlush + lane]; z = ws.bd[kFlush + lane]; }
         __syncwarp();
         if (lane < rest) { ws.bt[lane] = x; ws.bv[lane] = y; ws.bd[lane] = z; }
         __syncwarp();
@@ -251,11 +276,11 @@ __device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, ui
     if (pred) bv[cnt + __popc(mask & lanemask_lt())] = v;
     cnt += __popc(mask);
     __syncwarp();
-    if (cnt >= 32u) {
-        flush_ids(bv, 32u, list, counter);
-        const uint32_t rest = cnt - 32u;
+    if (cnt >= kFlush) {
+        flush_ids(bv, kFlush, list, counter);
+        const uint32_t rest = cnt - kFlush;
         uint32_t x = 0;
-        if (lane < rest) x = bv[32 + lane];
+        if (lane < rest) x = bv[kFlush + lane];
         __syncwarp();
         if (lane < rest) bv[lane] = x;
         __syncwarp();
@@ -374,6 +399,36 @@ __device__ void slot_entries_into_S(const SolveArgs &a, const PhaseDesc &d, Push
     }
 }
 
+// Classify the warp's improvement records 32 at a time (all of them when
+// `all`): each record runs relax(v, new distance) of Section III-C with its
+// stamp exchanges in flight together; fewer than 32 records stay buffered.
+template <int DT>
+__device__ __forceinline__ void classify_records(const SolveArgs &a, const BlockView &bvw, PushCnt &q, WarpStage &ws,
+                                                 uint32_t &nrec, uint32_t &ov_min, uint32_t &improved, bool all) {
+    const uint32_t lane = lane_id();
+    uint32_t start = 0;
+    // at most kRec / 32 chunks: nrec < kRec
+    for (uint32_t it = 0; it < kRec / 32u && (start + 32u <= nrec || (all && start < nrec)); ++it) {
+        const uint32_t idx = start + lane;
+        Push p{};
+        uint32_t v = 0;
+        if (idx < nrec) {
+            v = ws.iv[idx];
+            on_improved<DT>(a, bvw, v, ws.ik[idx], p, ov_min, improved);
+        }
+        stage_pushes(a, bvw.d, q, ws, p, v);
+        start += 32u;
+    }
+    const uint32_t rest = nrec > start ? nrec - start : 0u;     // fewer than 32
+    uint32_t x = 0, y = 0;
+    __syncwarp();
+    if (lane < rest) { x = ws.iv[start + lane]; y = ws.ik[start + lane]; }
+    __syncwarp();
+    if (lane < rest) { ws.iv[lane] = x; ws.ik[lane] = y; }
+    __syncwarp();
+    nrec = rest;
+}
+
 // LIGHT / HEAVY: relax the arcs of a list, split evenly over the warps.
 template <int DT, bool LIGHT>
 __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &acc, int *slot, WarpStage *stage,
@@ -388,7 +443,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
     const uint32_t E = d.arcs;
     const uint32_t T_lo = d.T_lo;
     uint32_t ov_min = inf_key<DT>();
-    uint32_t improved = 0;
+    uint32_t improved = 0, nrec = 0;
     PushCnt q{};
     WarpStage &ws = stage[threadIdx.x >> 5];
     if (from_slot) slot_entries_into_S(a, d, q, ws, gw, nw_all);
@@ -500,19 +555,32 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
                 const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
                 old[k] = (ck[k] < inf_key<DT>() && cand < cur[k]) ? atomicMin(a.packed + arc[k].x, cand) : 0ull;
             }
+            // strict distance decreases become records, classified 32 at a time
             #pragma unroll
             for (int k = 0; k < kIlp; ++k) {
-                Push p{};
                 const unsigned long long cand = ((unsigned long long)ck[k] << 32) | ov[k];
-                if (cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k])      // strict distance decrease
-                    on_improved<DT>(a, bvw, arc[k].x, ck[k], p, ov_min, improved);
-                stage_pushes(a, d, q, ws, p, arc[k].x);
+                const bool imp = cand < old[k] && (uint32_t)(old[k] >> 32) > ck[k];
+                const uint32_t mask = __ballot_sync(FULL, imp);
+                if (imp) {
+                    const uint32_t r = nrec + __popc(mask & lanemask_lt());
+                    ws.iv[r] = arc[k].x;
+                    ws.ik[r] = ck[k];
+                }
+                nrec += __popc(mask);
+            }
+            if (nrec >= 32u) {
+                __syncwarp();
+                classify_records<DT>(a, bvw, q, ws, nrec, ov_min, improved, false);
             }
         }
         if (lane == 0) {
             if (LIGHT) atomicAdd(&acc.arcs_light, (unsigned long long)(e1 - e0));
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
         }
+    }
+    if (nrec) {
+        __syncwarp();
+        classify_records<DT>(a, bvw, q, ws, nrec, ov_min, improved, true);
     }
     drain_pushes(a, d, q, ws);
     if (ov_min < inf_key<DT>()) atomicMin(&acc.ov_min, ov_min);
@@ -811,10 +879,13 @@ __device__ __forceinline__ void run_phase(const SolveArgs &a, const BlockView &v
     }
 }
 
+// The warps' staging buffers live in dynamic shared memory (blockDim / 32 of them).
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+
 template <int DT>
 __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
-    __shared__ WarpStage stage[kMaxWarps];
+    WarpStage *stage = reinterpret_cast<WarpStage *>(dyn_smem);
     __shared__ BlockView view;
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
@@ -870,7 +941,7 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(Solv
 template <int DT, uint32_t MODE>
 __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_phase(SolveArgs a) {
     __shared__ int slot[kMaxWarps * 32];
-    __shared__ WarpStage stage[kMaxWarps];
+    WarpStage *stage = reinterpret_cast<WarpStage *>(dyn_smem);
     __shared__ BlockView view;
     __shared__ BlockAcc acc;
     read_view(a.ctl, view);
@@ -972,22 +1043,53 @@ cudaError_t launch_init(const SolveArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+size_t stage_bytes(int block) { return (size_t)(block / 32) * sizeof(WarpStage); }
+
+// Allow the largest staging area on every kernel that uses it (once per device).
+cudaError_t allow_stage_smem() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return cudaSuccess;
+    const int bytes = (int)stage_bytes(512);
+    const void *fns[] = {
+        (const void *)k_solve_persistent<DSSSP_F32>, (const void *)k_solve_persistent<DSSSP_I32>,
+        (const void *)k_phase<DSSSP_F32, MODE_LIGHT>, (const void *)k_phase<DSSSP_I32, MODE_LIGHT>,
+        (const void *)k_phase<DSSSP_F32, MODE_HEAVY>, (const void *)k_phase<DSSSP_I32, MODE_HEAVY>,
+        (const void *)k_phase<DSSSP_F32, MODE_REBIN>, (const void *)k_phase<DSSSP_I32, MODE_REBIN>};
+    for (const void *f : fns)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return cudaSuccess;
+}
+
 cudaError_t solve_occupancy(int block, int *blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_persistent<DSSSP_F32>, block, 0);
+    cudaError_t e = allow_stage_smem();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_solve_persistent<DSSSP_F32>, block,
+                                                         stage_bytes(block));
 }
 
 cudaError_t launch_solve_persistent(const SolveArgs &a, int grid, int block, cudaStream_t st) {
     void *args[] = {(void *)&a};
     const void *fn = a.dtype == DSSSP_F32 ? (const void *)k_solve_persistent<DSSSP_F32>
                                           : (const void *)k_solve_persistent<DSSSP_I32>;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, 0, st);
+    cudaError_t e = allow_stage_smem();
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, stage_bytes(block), st);
 }
 
 cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, int block, cudaStream_t st) {
+    cudaError_t e = allow_stage_smem();
+    if (e != cudaSuccess) return e;
+    const size_t sb = stage_bytes(block);
 #define DSSSP_PHASE_CASE(M)                                                              \
     case M:                                                                              \
-        if (a.dtype == DSSSP_F32) k_phase<DSSSP_F32, M><<<grid, block, 0, st>>>(a);      \
-        else k_phase<DSSSP_I32, M><<<grid, block, 0, st>>>(a);                          \
+        if (a.dtype == DSSSP_F32) k_phase<DSSSP_F32, M><<<grid, block, sb, st>>>(a);     \
+        else k_phase<DSSSP_I32, M><<<grid, block, sb, st>>>(a);                         \
         break;
     switch (mode) {
         DSSSP_PHASE_CASE(MODE_LIGHT)
