@@ -142,43 +142,41 @@ __device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32
     if (lane + 32u < n) list[base + lane + 32u] = bv[lane + 32u];
 }
 
-// Append n <= 32 staged slot entries: lanes are grouped by (slot, list) and
-// each group takes one atomic on its slot's counter.
+// Append n <= 32 staged slot entries: lanes are grouped by (slot, list); the
+// leader of every group takes its slot counter with one atomic, all groups at
+// once, and each lane finds its place from its rank and the arc counts of the
+// lower lanes of its group.
 __device__ __forceinline__ void flush_slot_entries32(const SolveArgs &a, const uint32_t *bt, const uint32_t *bv,
                                                      const uint32_t *bd, uint32_t n) {
     const uint32_t lane = lane_id();
     const bool has = lane < n;
     const uint32_t t = has ? bt[lane] : 0u, v = has ? bv[lane] : 0u, d = has ? bd[lane] : 0u;
-    const uint32_t key = (t << 1) | (d == 0u ? 1u : 0u);
-    uint32_t todo = __ballot_sync(FULL, has);
-    Ctl *c = a.ctl;
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const uint32_t lkey = __shfl_sync(FULL, key, leader);
-        const uint32_t grp = __ballot_sync(FULL, has && key == lkey);
-        todo &= ~grp;
-        const bool mine = (grp >> lane) & 1u;
-        const uint32_t slot = lkey >> 1;
-        const uint32_t rank = __popc(grp & lanemask_lt());
-        if (lkey & 1u) {                                   // heavy-only list of the slot
-            uint32_t base = 0;
-            if ((int)lane == leader) base = atomicAdd(&c->nSH[slot], (uint32_t)__popc(grp));
-            base = __shfl_sync(FULL, base, leader);
-            if (mine) a.SH[(size_t)slot * a.n + base + rank] = v;
-        } else {                                           // arc list of the slot
-            const uint32_t dd = mine ? d : 0u;
-            uint32_t incl = dd;
-            #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t x = __shfl_up_sync(FULL, incl, o);
-                if ((int)lane >= o) incl += x;
-            }
-            const uint32_t tot = __shfl_sync(FULL, incl, 31);
-            unsigned long long old = 0;
-            if ((int)lane == leader) old = atomicAdd(&c->ctrSL[slot], ((unsigned long long)__popc(grp) << 32) | tot);
-            old = __shfl_sync(FULL, old, leader);
-            if (mine) a.SL[(size_t)slot * a.n + (uint32_t)(old >> 32) + rank] = make_uint2(v, (uint32_t)old + incl - dd);
+    const uint32_t key = has ? ((t << 1) | (d == 0u ? 1u : 0u)) : 0xFFFFFFFFu;
+    const uint32_t grp = __match_any_sync(FULL, key);
+    const uint32_t below = grp & lanemask_lt();
+    const bool leader = below == 0u;
+    const uint32_t rank = __popc(below);
+    // arc count of the group's lower lanes (excl) and of the whole group (tot)
+    uint32_t excl = 0, tot = 0;
+    #pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const uint32_t dj = __shfl_sync(FULL, d, j);
+        if ((grp >> j) & 1u) {
+            tot += dj;
+            if ((uint32_t)j < lane) excl += dj;
         }
+    }
+    const uint32_t slot = t;
+    Ctl *c = a.ctl;
+    unsigned long long old = 0;
+    if (has && leader) {
+        if (key & 1u) old = atomicAdd(&c->nSH[slot], (uint32_t)__popc(grp));          // heavy-only list
+        else old = atomicAdd(&c->ctrSL[slot], ((unsigned long long)__popc(grp) << 32) | tot);
+    }
+    old = __shfl_sync(FULL, old, __ffs(grp) - 1);
+    if (has) {
+        if (key & 1u) a.SH[(size_t)slot * a.n + (uint32_t)old + rank] = v;
+        else a.SL[(size_t)slot * a.n + (uint32_t)(old >> 32) + rank] = make_uint2(v, (uint32_t)old + excl);
     }
 }
 
