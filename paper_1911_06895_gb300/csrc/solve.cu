@@ -47,6 +47,10 @@ constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 #endif
 constexpr int kIlp = DSSSP_ILP;        // independent 32-arc steps per warp iteration
 constexpr uint32_t kMinSlice = 32u * kIlp;
+#ifndef DSSSP_ENTRY_COST
+#define DSSSP_ENTRY_COST 4
+#endif
+constexpr uint32_t kEntryCost = DSSSP_ENTRY_COST;   // arcs' worth of work per list entry (merge-path weight)
 constexpr uint32_t kNoSlot = kSlots;
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
@@ -445,27 +449,54 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
     PushCnt q{};
     WarpStage &ws = stage[threadIdx.x >> 5];
     if (from_slot) slot_entries_into_S(a, d, q, ws, gw, nw_all);
-    // at least kMinSlice arcs per warp: small phases use few warps
-    const uint32_t want_w = (E + kMinSlice - 1u) / kMinSlice;
-    const uint32_t nw = want_w < nw_all ? want_w : nw_all;
+    // Merge-path over the list's entries and arcs together: an entry costs
+    // kEntryCost arcs' worth of work (its share of a window load and of the owner
+    // mapping), so a slice of many short segments gets fewer arcs. In merged
+    // order the first arc of entry i sits at (i + 1) * kEntryCost + offs[i]; at
+    // least kMinSlice units per warp (small phases use few warps).
+    const unsigned long long W = (unsigned long long)count * kEntryCost + E;
+    const unsigned long long want_w = (W + kMinSlice - 1u) / kMinSlice;
+    const uint32_t nw = want_w < (unsigned long long)nw_all ? (uint32_t)want_w : nw_all;
     if (gw < nw) {
-        const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
-        const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
-        // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
-        uint32_t lo = 0, hi = count;
-        while (hi - lo > 32u) {
-            const uint32_t step = (hi - lo + 31u) >> 5;
-            const uint32_t p = lo + lane * step;
-            const bool ok = p < hi && __ldcg(offs + 2ull * p) <= e0;
-            const uint32_t k = 31u - __clz(__ballot_sync(FULL, ok));
-            lo += k * step;
-            hi = min(hi, lo + step);
+        const unsigned long long d0 = W * gw / nw, d1 = W * (gw + 1) / nw;
+        // i0 / i1 = number of entries whose first arc lies at or before d0 / d1:
+        // two 32-ary searches in step, down to fewer than 32 candidates each
+        uint32_t lo0 = 0, hi0 = count, lo1 = 0, hi1 = count;
+        while (hi0 - lo0 > 31u || hi1 - lo1 > 31u) {
+            const uint32_t st0 = (hi0 - lo0 + 31u) >> 5, st1 = (hi1 - lo1 + 31u) >> 5;
+            const uint32_t p0 = lo0 + lane * st0, p1 = lo1 + lane * st1;
+            const bool ok0 = hi0 - lo0 > 31u && p0 < hi0 &&
+                             (unsigned long long)(p0 + 1u) * kEntryCost + __ldcg(offs + 2ull * p0) <= d0;
+            const bool ok1 = hi1 - lo1 > 31u && p1 < hi1 &&
+                             (unsigned long long)(p1 + 1u) * kEntryCost + __ldcg(offs + 2ull * p1) <= d1;
+            const uint32_t k0 = __popc(__ballot_sync(FULL, ok0)), k1 = __popc(__ballot_sync(FULL, ok1));
+            if (hi0 - lo0 > 31u) {
+                hi0 = min(hi0, lo0 + k0 * st0);
+                lo0 = k0 ? lo0 + (k0 - 1u) * st0 + 1u : lo0;
+            }
+            if (hi1 - lo1 > 31u) {
+                hi1 = min(hi1, lo1 + k1 * st1);
+                lo1 = k1 ? lo1 + (k1 - 1u) * st1 + 1u : lo1;
+            }
         }
+        // final round: lane j probes lo + j (up to hi inclusive) and keeps its offset
+        uint32_t i0, i1, o0, o1;
         {
-            const uint32_t p = lo + lane;
-            const bool ok = p < hi && __ldcg(offs + 2ull * p) <= e0;
-            lo += 31u - __clz(__ballot_sync(FULL, ok));
+            const uint32_t p0 = lo0 + lane, p1 = lo1 + lane;
+            const uint32_t v0 = p0 <= hi0 ? (p0 < count ? __ldcg(offs + 2ull * p0) : E) : E;
+            const uint32_t v1 = p1 <= hi1 ? (p1 < count ? __ldcg(offs + 2ull * p1) : E) : E;
+            const bool ok0 = p0 < hi0 && (unsigned long long)(p0 + 1u) * kEntryCost + v0 <= d0;
+            const bool ok1 = p1 < hi1 && (unsigned long long)(p1 + 1u) * kEntryCost + v1 <= d1;
+            const uint32_t k0 = __popc(__ballot_sync(FULL, ok0)), k1 = __popc(__ballot_sync(FULL, ok1));
+            i0 = lo0 + k0;
+            i1 = lo1 + k1;
+            o0 = __shfl_sync(FULL, v0, k0);          // offset of entry i0 (E when i0 == count)
+            o1 = __shfl_sync(FULL, v1, k1);
         }
+        const uint32_t e0 = (uint32_t)min(d0 - (unsigned long long)i0 * kEntryCost, (unsigned long long)o0);
+        const uint32_t e1 = (uint32_t)min(d1 - (unsigned long long)i1 * kEntryCost, (unsigned long long)o1);
+        // the entry owning arc e0
+        const uint32_t lo = (i0 < count && e0 == o0) ? i0 : i0 - 1u;
         // window: lane k holds entry jw + k; wend = arc offset just past the window.
         // A stale slot entry (its vertex moved to a lower bucket) gets key INF and is skipped.
         uint32_t jw = lo, wv = 0, woff = 0xFFFFFFFFu, wbeg = 0, wkey = inf_key<DT>(), wend = 0;
