@@ -127,10 +127,17 @@ struct TeamShared {
     uint32_t mode, cur, scur, xcur, pstamp, sst, T, T_lo, fst, gen, inst;
 };
 
+// Improved vertices wait in a per-warp record buffer and are classified 32 at
+// a time (their stamp exchanges in flight together).
+constexpr uint32_t kTRec = 32 + 32 * kTIlp;
+// A list entry weighs this many arcs in the merge-path split of a phase.
+constexpr uint32_t kTEntryCost = 4;
+
 struct TStage {
-    uint32_t fv[64], fd[64];   // next frontier (vertex, light degree)
-    uint32_t sv[64], sd[64];   // S (vertex, heavy degree)
-    uint32_t xv[64];           // far list
+    uint32_t fv[wu::kStage], fd[wu::kStage];   // next frontier (vertex, light degree)
+    uint32_t sv[wu::kStage], sd[wu::kStage];   // S (vertex, heavy degree)
+    uint32_t xv[wu::kStage];                   // far list
+    uint32_t iv[kTRec], ik[kTRec];             // improvement records (vertex, new key)
 };
 
 struct Team {
@@ -186,6 +193,36 @@ __device__ __forceinline__ void on_improved(const Team &t, const TeamShared &s, 
     }
 }
 
+// Classify the warp's improvement records 32 at a time (all of them when
+// `all`); fewer than 32 stay buffered.
+template <int DT>
+__device__ __forceinline__ void team_classify(const Team &t, const TeamShared &s, TStage &ws, uint32_t &nf,
+                                              uint32_t &ns, uint32_t &nx, uint32_t &nrec, uint32_t &far_min,
+                                              bool all) {
+    const uint32_t lane = lane_id();
+    uint32_t start = 0;
+    // at most kTRec / 32 chunks: nrec < kTRec
+    for (uint32_t it = 0; it < kTRec / 32u && (start + 32u <= nrec || (all && start < nrec)); ++it) {
+        const uint32_t idx = start + lane;
+        TPush p{};
+        uint32_t v = 0;
+        if (idx < nrec) {
+            v = ws.iv[idx];
+            on_improved<DT>(t, s, v, ws.ik[idx], p, far_min);
+        }
+        stage_push(s.ph, ws, nf, ns, nx, p, v);
+        start += 32u;
+    }
+    const uint32_t rest = nrec > start ? nrec - start : 0u;
+    uint32_t x = 0, y = 0;
+    __syncwarp();
+    if (lane < rest) { x = ws.iv[start + lane]; y = ws.ik[start + lane]; }
+    __syncwarp();
+    if (lane < rest) { ws.iv[lane] = x; ws.ik[lane] = y; }
+    __syncwarp();
+    nrec = rest;
+}
+
 // LIGHT / HEAVY: relax the arcs of one list, split evenly over the team's warps
 // (merge-path over the entries' arc offsets; 32-entry window per warp).
 template <int DT, bool LIGHT, bool TAPE>
@@ -196,26 +233,48 @@ __device__ void team_relax(const Team &t, const TeamShared &s, const uint2 *list
     const uint32_t lane = lane_id();
     const uint32_t gw = threadIdx.x >> 5, nw_all = blockDim.x >> 5;
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[2 * j]
-    uint32_t nf = 0, ns = 0, nx = 0;
-    const uint32_t want_w = (E + kTMinSlice - 1u) / kTMinSlice;
-    const uint32_t nw = want_w < nw_all ? want_w : nw_all;
+    uint32_t nf = 0, ns = 0, nx = 0, nrec = 0;
+    // merge-path over entries and arcs together (an entry weighs kTEntryCost arcs);
+    // the first arc of entry i sits at (i + 1) * kTEntryCost + offs[i]
+    const unsigned long long W = (unsigned long long)count * kTEntryCost + E;
+    const unsigned long long want_w = (W + kTMinSlice - 1u) / kTMinSlice;
+    const uint32_t nw = want_w < (unsigned long long)nw_all ? (uint32_t)want_w : nw_all;
     if (gw < nw) {
-        const uint32_t e0 = (uint32_t)(((unsigned long long)E * gw) / nw);
-        const uint32_t e1 = (uint32_t)(((unsigned long long)E * (gw + 1)) / nw);
-        // last entry whose offset is <= e0 (32-ary search; entry lo always qualifies)
-        uint32_t lo = 0, hi = count;
-        while (hi - lo > 32u) {
-            const uint32_t step = (hi - lo + 31u) >> 5;
-            const uint32_t q = lo + lane * step;
-            const bool ok = q < hi && __ldcg(offs + 2ull * q) <= e0;
-            lo += (31u - __clz(__ballot_sync(FULL, ok))) * step;
-            hi = min(hi, lo + step);
+        const unsigned long long d0 = W * gw / nw, d1 = W * (gw + 1) / nw;
+        uint32_t lo0 = 0, hi0 = count, lo1 = 0, hi1 = count;
+        while (hi0 - lo0 > 31u || hi1 - lo1 > 31u) {
+            const uint32_t st0 = (hi0 - lo0 + 31u) >> 5, st1 = (hi1 - lo1 + 31u) >> 5;
+            const uint32_t p0 = lo0 + lane * st0, p1 = lo1 + lane * st1;
+            const bool ok0 = hi0 - lo0 > 31u && p0 < hi0 &&
+                             (unsigned long long)(p0 + 1u) * kTEntryCost + __ldcg(offs + 2ull * p0) <= d0;
+            const bool ok1 = hi1 - lo1 > 31u && p1 < hi1 &&
+                             (unsigned long long)(p1 + 1u) * kTEntryCost + __ldcg(offs + 2ull * p1) <= d1;
+            const uint32_t k0 = __popc(__ballot_sync(FULL, ok0)), k1 = __popc(__ballot_sync(FULL, ok1));
+            if (hi0 - lo0 > 31u) {
+                hi0 = min(hi0, lo0 + k0 * st0);
+                lo0 = k0 ? lo0 + (k0 - 1u) * st0 + 1u : lo0;
+            }
+            if (hi1 - lo1 > 31u) {
+                hi1 = min(hi1, lo1 + k1 * st1);
+                lo1 = k1 ? lo1 + (k1 - 1u) * st1 + 1u : lo1;
+            }
         }
+        uint32_t i0, i1, o0, o1;
         {
-            const uint32_t q = lo + lane;
-            const bool ok = q < hi && __ldcg(offs + 2ull * q) <= e0;
-            lo += 31u - __clz(__ballot_sync(FULL, ok));
+            const uint32_t p0 = lo0 + lane, p1 = lo1 + lane;
+            const uint32_t v0 = p0 <= hi0 ? (p0 < count ? __ldcg(offs + 2ull * p0) : E) : E;
+            const uint32_t v1 = p1 <= hi1 ? (p1 < count ? __ldcg(offs + 2ull * p1) : E) : E;
+            const bool ok0 = p0 < hi0 && (unsigned long long)(p0 + 1u) * kTEntryCost + v0 <= d0;
+            const bool ok1 = p1 < hi1 && (unsigned long long)(p1 + 1u) * kTEntryCost + v1 <= d1;
+            const uint32_t k0 = __popc(__ballot_sync(FULL, ok0)), k1 = __popc(__ballot_sync(FULL, ok1));
+            i0 = lo0 + k0;
+            i1 = lo1 + k1;
+            o0 = __shfl_sync(FULL, v0, k0);
+            o1 = __shfl_sync(FULL, v1, k1);
         }
+        const uint32_t e0 = (uint32_t)min(d0 - (unsigned long long)i0 * kTEntryCost, (unsigned long long)o0);
+        const uint32_t e1 = (uint32_t)min(d1 - (unsigned long long)i1 * kTEntryCost, (unsigned long long)o1);
+        const uint32_t lo = (i0 < count && e0 == o0) ? i0 : i0 - 1u;
         // window: lane k holds entry jw + k; wend = arc offset just past the window
         uint32_t jw = lo, wv = 0, woff = 0xFFFFFFFFu, wbeg = 0, wkey = inf_key<DT>(), wend = 0;
         auto load_window = [&](uint32_t j) {
@@ -298,15 +357,26 @@ __device__ void team_relax(const Team &t, const TeamShared &s, const uint2 *list
                 old[k] = (ck[k] < inf_key<DT>() && cand[k] < cur[k]) ? atomicMin(t.packed + arc[k].x, cand[k]) : 0ull;
             #pragma unroll
             for (int k = 0; k < kTIlp; ++k) {
-                TPush p{};
-                if (cand[k] < old[k] && (uint32_t)(old[k] >> 32) > ck[k]) {      // strict distance decrease
-                    ++improved;
-                    on_improved<DT>(t, s, arc[k].x, ck[k], p, far_min);
+                const bool imp = cand[k] < old[k] && (uint32_t)(old[k] >> 32) > ck[k];   // strict decrease
+                const uint32_t mask = __ballot_sync(FULL, imp);
+                if (imp) {
+                    const uint32_t r = nrec + __popc(mask & wu::lanemask_lt());
+                    ws.iv[r] = arc[k].x;
+                    ws.ik[r] = ck[k];
                 }
-                stage_push(ph, ws, nf, ns, nx, p, arc[k].x);
+                nrec += __popc(mask);
+                if (imp) ++improved;
+            }
+            if (nrec >= 32u) {
+                __syncwarp();
+                team_classify<DT>(t, s, ws, nf, ns, nx, nrec, far_min, false);
             }
         }
         if (lane == 0) relaxed += e1 - e0;
+    }
+    if (nrec) {
+        __syncwarp();
+        team_classify<DT>(t, s, ws, nf, ns, nx, nrec, far_min, true);
     }
     drain_push(ph, ws, nf, ns, nx);
 }
