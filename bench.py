@@ -225,11 +225,16 @@ def main():
                     help="skip the batched and forward+backward comparisons")
     ap.add_argument("--profile-solves", type=int, default=0,
                     help="profiling driver: run this many solves at --profile-delta and exit (for ncu)")
+    ap.add_argument("--profile-batch", type=int, default=0,
+                    help="profiling driver: one batch of this many scale-20 R-MAT sources at --profile-delta")
     ap.add_argument("--profile-delta", default="0.1",
                     help="comma-separated Deltas, or 'all' for every Delta of the sweep")
     args = ap.parse_args()
     if args.profile_solves:
         profile_driver(args)
+        return
+    if args.profile_batch:
+        profile_batch_driver(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -394,6 +399,12 @@ def _events_ms(torch, fn, reps: int, stream=None) -> float:
     return statistics.median(ts)
 
 
+def batch_algorithmic_bytes(stats, ns) -> int:
+    """Algorithmic bytes of a batch run from its per-instance counters (same per-unit figures)."""
+    return sum(B_VERTEX * (st["vertices_light"] + st["vertices_heavy"]) + B_ARC * (st["arcs_light"] + st["arcs_heavy"])
+               + B_FAR * st["far_scanned"] + B_INIT_UNPACK * n for st, n in zip(stats, ns))
+
+
 def run_extras(ds, torch):
     """Batched and forward+backward throughput against the plain per-source solve on the
     same GPU: (a) 256 sources on a scale-20 R-MAT in one launch, (b) 512 ER graphs of
@@ -413,8 +424,10 @@ def run_extras(ds, torch):
     tune_s = time.perf_counter() - t
     b = ds.Batch(h, [d_b], srcs)
     ms_b = _events_ms(torch, b.run, 3)
-    b.sync()
+    bst = b.sync(stats=True)
     b.close()
+    peak, _ = measured_peak_gbs()
+    gbs_a = batch_algorithmic_bytes(bst, [g.n] * len(srcs)) / (ms_b * 1e-3) / 1e9
 
     def plain_a():
         for s in srcs:
@@ -425,7 +438,8 @@ def run_extras(ds, torch):
     out["batched"]["rmat20_unit_256src"] = {
         "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "ms": ms_b,
         "gteps": g.m * len(srcs) / (ms_b * 1e-3) / 1e9, "plain_delta": d_p, "plain_ms": ms_p,
-        "plain_gteps": g.m * len(srcs) / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s}
+        "plain_gteps": g.m * len(srcs) / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s,
+        "algorithmic_gbs": gbs_a, "hbm_frac": gbs_a / peak}
 
     # (b) many graphs of uneven sizes
     fam = W.er_family()
@@ -437,8 +451,9 @@ def run_extras(ds, torch):
     tune_s = time.perf_counter() - t
     b = ds.Batch(hs, deltas, fsrc, src_graph=list(range(len(fam))))
     ms_b = _events_ms(torch, b.run, 3)
-    b.sync()
+    bst = b.sync(stats=True)
     b.close()
+    gbs_b = batch_algorithmic_bytes(bst, [x.n for x, _ in fam]) / (ms_b * 1e-3) / 1e9
     for hh, d in zip(hs, deltas):
         hh.prepare(d)
 
@@ -452,7 +467,8 @@ def run_extras(ds, torch):
     out["batched"]["er512"] = {
         "graphs": len(fam), "sum_n": sum(x.n for x, _ in fam), "sum_m": msum,
         "delta_range": [min(deltas), max(deltas)], "ms": ms_b, "gteps": msum / (ms_b * 1e-3) / 1e9,
-        "plain_ms": ms_p, "plain_gteps": msum / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s}
+        "plain_ms": ms_p, "plain_gteps": msum / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s,
+        "algorithmic_gbs": gbs_b, "hbm_frac": gbs_b / peak}
 
     # (c) forward + backward
     g, srcs, c = W.rmat20_lognormal()
@@ -488,7 +504,56 @@ def run_extras(ds, torch):
         "bwd_ms": ms_bw, "fwd_bwd_gteps": sm / (ms_fb * 1e-3) / 1e9, "fwd_gteps": sm / (ms_f * 1e-3) / 1e9,
         "plain_solve_ms": ms_p, "plain_solve_gteps": sm / (ms_p * 1e-3) / 1e9,
         "fwd_bwd_over_fwd": ms_fb / ms_f, "tune_s": tune_s}
+
+    # (d) ablation: the paper's dense-vector form (t_Bi and S as per-vertex stamps scanned
+    # in full every phase, dsssp_solve_noalloc) against the list-based solve, scale-17 R-MAT
+    g, srcs, _ = W.rmat22_unit(scale=17, n_sources=8)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    cl = torch.from_numpy(g.col).cuda()
+    ww = torch.from_numpy(g.w).cuda()
+    h = ds.Graph(rp, cl, ww)
+    dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    abl = {}
+    for d in (0.05, 0.1, 0.5):
+        h.prepare(d)
+
+        def dense():
+            for s in srcs:
+                ds.check(ds.dsssp_solve_noalloc(g.n, g.m, rp.data_ptr(), cl.data_ptr(), ww.data_ptr(), ds.DSSSP_F32,
+                                                s, d, dist.data_ptr(), pred.data_ptr(),
+                                                ds._stream_ptr(stream)), "dsssp_solve_noalloc")
+
+        def lists():
+            for s in srcs:
+                h.solve(s, d, dist=dist, pred=pred, options=o_async)
+        ms_d = _events_ms(torch, dense, 1) / len(srcs)
+        ms_l = _events_ms(torch, lists, 1) / len(srcs)
+        h.sync()
+        abl[str(d)] = {"dense_ms_per_solve": ms_d, "list_ms_per_solve": ms_l, "list_speedup": ms_d / ms_l}
+    h.close()
+    out["ablation_dense_vs_lists"] = {"workload": f"rmat17_unit n={g.n} m={g.m}, 8 sources", "per_delta": abl}
     return out
+
+
+def profile_batch_driver(args):
+    """One batch of K sources on the scale-20 R-MAT (fp32 U[0,1)), for profilers."""
+    import torch
+    import paper_1911_06895_gb300 as ds
+    import graphgen.workloads as W
+    g, srcs = W.rmat20_unit(n_sources=max(args.profile_batch, 1))
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    d = float(args.profile_delta)
+    b = ds.Batch(h, [d], srcs[:args.profile_batch])
+    b.run()
+    st = b.sync(stats=True)
+    nbytes = batch_algorithmic_bytes(st, [g.n] * len(st))
+    print(json.dumps({"instances": len(st), "delta": d, "algorithmic_bytes": nbytes,
+                      "arcs": sum(x["arcs_light"] + x["arcs_heavy"] for x in st),
+                      "max_instance_ms": max(x["ns"] for x in st) / 1e6}), flush=True)
+    b.close()
+    torch.cuda.synchronize()
 
 
 def profile_driver(args):

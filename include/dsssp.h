@@ -233,7 +233,9 @@ typedef struct {
     int64_t far_scanned;      /* far-list entries examined by selections                        */
     int64_t ns;               /* device time from the instance's start to its end              */
     int64_t team;             /* block that solved it                                           */
-    int64_t reserved[6];
+    int64_t vertices_light;   /* sum of |frontier| over light rounds                           */
+    int64_t vertices_heavy;   /* sum of |S| over heavy passes                                   */
+    int64_t reserved[4];
 } dsssp_batch_stats;
 
 /* Build a batch (a plan of n_inst solves):

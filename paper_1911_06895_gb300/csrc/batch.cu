@@ -55,7 +55,7 @@ enum TMode : uint32_t { T_LIGHT = 0, T_HEAVY = 1, T_SELECT = 2, T_DONE = 3 };
 
 enum BStat {
     BS_BUCKETS = 0, BS_LIGHT, BS_HEAVY, BS_SELECT, BS_ALIGHT, BS_AHEAVY, BS_IMPROVE, BS_FARSCAN, BS_NS, BS_TEAM,
-    kBStats = 16
+    BS_VLIGHT, BS_VHEAVY, kBStats = 16
 };
 
 struct BGraphDev {
@@ -119,7 +119,7 @@ struct TeamShared {
     uint32_t *nstamp, *sstamp, *fflag;
     unsigned long long ctrF[2], ctrS[2];     // (entries << 32) | arcs
     unsigned long long a_light, a_heavy, improve, far_scanned;
-    long long phases, n_light, n_heavy, n_select, buckets;
+    long long phases, n_light, n_heavy, n_select, buckets, v_light, v_heavy;
     unsigned long long t0;
     uint32_t nX[2];
     uint32_t far_min;                        // <= every key of a live far entry
@@ -429,11 +429,13 @@ __device__ __noinline__ void team_decide(TeamShared &s, const BGraphDev &g, cons
     switch (s.mode) {
     case T_LIGHT:
         s.n_light += 1;
+        s.v_light += (long long)(s.ctrF[s.cur] >> 32);
         s.ctrF[s.cur] = 0ull;
         s.cur ^= 1u;
         break;
     case T_HEAVY:
         s.n_heavy += 1;
+        s.v_heavy += (long long)(s.ctrS[s.scur] >> 32);
         s.ctrS[s.scur] = 0ull;
         s.scur ^= 1u;                        // S pushed during the heavy pass (re-opened bucket)
         s.cur ^= 1u;
@@ -539,7 +541,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             s.t0 = wu::globaltimer();
             s.ctrF[0] = s.ctrF[1] = s.ctrS[0] = s.ctrS[1] = 0ull;
             s.a_light = s.a_heavy = s.improve = s.far_scanned = 0ull;
-            s.phases = s.n_light = s.n_heavy = s.n_select = 0;
+            s.phases = s.n_light = s.n_heavy = s.n_select = s.v_light = s.v_heavy = 0;
             s.buckets = 1;
             s.nX[0] = s.nX[1] = 0u;
             s.far_min = inf_key<DT>();
@@ -636,6 +638,8 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             st[BS_FARSCAN] = (long long)s.far_scanned;
             st[BS_NS] = (long long)(wu::globaltimer() - s.t0);
             st[BS_TEAM] = blockIdx.x;
+            st[BS_VLIGHT] = s.v_light;
+            st[BS_VHEAVY] = s.v_heavy;
         }
         __syncthreads();
     }
@@ -1080,6 +1084,8 @@ dsssp_status dsssp_batch_sync(dsssp_batch *b, dsssp_batch_stats *stats, void *st
             o.far_scanned = x[BS_FARSCAN];
             o.ns = x[BS_NS];
             o.team = x[BS_TEAM];
+            o.vertices_light = x[BS_VLIGHT];
+            o.vertices_heavy = x[BS_VHEAVY];
         }
     }
     return (dsssp_status)err;

@@ -71,7 +71,8 @@ class dsssp_stats(ctypes.Structure):
 class dsssp_batch_stats(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int64) for name in (
         "buckets", "light_phases", "heavy_phases", "select_phases", "arcs_light", "arcs_heavy",
-        "improvements", "far_scanned", "ns", "team")] + [("reserved", ctypes.c_int64 * 6)]
+        "improvements", "far_scanned", "ns", "team", "vertices_light", "vertices_heavy")] + [
+        ("reserved", ctypes.c_int64 * 4)]
 
     def as_dict(self) -> dict:
         return {name: int(getattr(self, name)) for name, _ in self._fields_ if name != "reserved"}
