@@ -92,7 +92,9 @@ typedef struct {
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
-    int32_t  reserved[5];
+    int32_t  team_blocks;   /* batches: blocks per instance (a thread-block cluster of 1, 2, 4 or 8);
+                               0 = automatic (more blocks per instance when instances are few)   */
+    int32_t  reserved[4];
 } dsssp_options;
 
 /* Counters of one solve (filled when a non-NULL pointer is passed; this makes
@@ -207,7 +209,8 @@ dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, c
 /* or many graphs -- add a second, coarser dimension. A batch solves every   */
 /* instance with the same method and the same exact results as dsssp_solve;  */
 /* each instance keeps its own bucket state and is processed start to end by */
-/* one block of a persistent kernel that takes instances from a device-side  */
+/* one team -- a block, or a thread-block cluster of up to 8 blocks -- of a  */
+/* persistent kernel whose teams take instances from a device-side           */
 /* queue (largest graphs first). A batch is a plan: its instance table,      */
 /* working memory and a CUDA graph of its launch are built once, then run    */
 /* any number of times.                                                     */
@@ -249,7 +252,9 @@ typedef struct {
  *   pred        HOST array of n_inst DEVICE pointers (int32[n]) or NULL entries, or NULL;
  *   flags       DSSSP_BATCH_TAPE or 0;
  *   opt         NULL, or options (block_size must be 512 or 0; grid_size caps the number of
- *               blocks; max_phases caps the phases of each instance);
+ *               blocks; max_phases caps the phases of each instance; team_blocks sets how many
+ *               blocks -- a thread-block cluster sharing the instance's control through
+ *               distributed shared memory -- solve one instance: 1, 2, 4, 8, or 0 for automatic);
  *   stream      orders the set-up work (light/heavy splits, tables); the call waits for it;
  *   out         receives the plan.
  * The plan keeps the graphs' splits for these Deltas alive (a graph holds at most four) and

@@ -29,6 +29,7 @@
 // round's ready list depends only on earlier rounds (a topological order of
 // the predecessor tree, whatever order the forward run found the distances in).
 #include <algorithm>
+#include <cooperative_groups.h>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -40,6 +41,7 @@
 namespace dsssp {
 namespace {
 
+namespace cg = cooperative_groups;
 using wu::FULL;
 using wu::inf_key;
 using wu::key_add;
@@ -99,15 +101,24 @@ struct BatchArgs {
     long long max_phases;
 };
 
-// Destinations and thresholds of one phase (uniform over the block).
+// One block's view of the current phase, in its own shared memory: the list the
+// phase reads, where its pushes go, and the team counters (in the leader block's
+// shared memory, reached through distributed shared memory when the team is a
+// cluster of several blocks).
 struct Ph {
-    uint2 *Fo;
+    uint2 *Fo;                      // next frontier
     unsigned long long *cF;
-    uint2 *So;
+    uint2 *So;                      // S pushes
     unsigned long long *cS;
-    uint32_t *Xo;
+    uint32_t *Xo;                   // far-list pushes
     uint32_t *cX;
-    uint32_t T, T_lo, pstamp, sst, fst;
+    const uint2 *in;                // LIGHT / HEAVY: the list read
+    const uint32_t *xin;            // SELECT: the far list read
+    uint32_t count, arcs;           // its entries and arcs
+    uint32_t *nstamp, *sstamp, *fflag;
+    uint32_t *far_min, *next_min;   // team reductions
+    unsigned long long *improve, *a_light, *a_heavy;
+    uint32_t T, T_lo, pstamp, sst, fst, mode;
 };
 
 // Team control in shared memory. Thread 0 decides the next phase between two
@@ -115,7 +126,6 @@ struct Ph {
 struct TeamShared {
     BInstDev I;                              // the instance being solved and its graph
     BGraphDev G;
-    Ph ph;                                   // the current phase's destinations
     uint32_t *nstamp, *sstamp, *fflag;
     unsigned long long ctrF[2], ctrS[2];     // (entries << 32) | arcs
     unsigned long long a_light, a_heavy, improve, far_scanned;
@@ -125,6 +135,7 @@ struct TeamShared {
     uint32_t far_min;                        // <= every key of a live far entry
     uint32_t next_min;                       // SELECT: smallest key kept
     uint32_t mode, cur, scur, xcur, pstamp, sst, T, T_lo, fst, gen, inst;
+    uint32_t gen_seen;                       // every block: the leader's generator at instance start
 };
 
 // Improved vertices wait in a per-warp record buffer and are classified 32 at
@@ -172,31 +183,30 @@ __device__ __forceinline__ void drain_push(const Ph &ph, TStage &ws, uint32_t &n
 // back into bucket i (once per phase into F, once per S round into S), or
 // into a later bucket (once into the far list while it has a live entry).
 template <int DT>
-__device__ __forceinline__ void on_improved(const Team &t, const TeamShared &s, uint32_t v, uint32_t ck, TPush &p,
+__device__ __forceinline__ void on_improved(const Team &t, const Ph &ph, uint32_t v, uint32_t ck, TPush &p,
                                             uint32_t &far_min) {
-    const Ph &ph = s.ph;
     if (ck < ph.T) {
-        const uint32_t prev = atomicExch(s.nstamp + v, ph.pstamp);
+        const uint32_t prev = atomicExch(ph.nstamp + v, ph.pstamp);
         const uint4 vi = t.vinfo[v];
-        const uint32_t ss = __ldcg(s.sstamp + v);
+        const uint32_t ss = __ldcg(ph.sstamp + v);
         if (prev == ph.pstamp) return;
         p.fdeg = vi.y - vi.x;
         p.f = p.fdeg != 0u;
         if (ss != ph.sst) {
-            s.sstamp[v] = ph.sst;
+            ph.sstamp[v] = ph.sst;
             p.sdeg = vi.z - vi.y;
             p.s = p.sdeg != 0u;
         }
     } else {
         far_min = min(far_min, ck);
-        p.x = atomicExch(s.fflag + v, ph.fst) != ph.fst;
+        p.x = atomicExch(ph.fflag + v, ph.fst) != ph.fst;
     }
 }
 
 // Classify the warp's improvement records 32 at a time (all of them when
 // `all`); fewer than 32 stay buffered.
 template <int DT>
-__device__ __forceinline__ void team_classify(const Team &t, const TeamShared &s, TStage &ws, uint32_t &nf,
+__device__ __forceinline__ void team_classify(const Team &t, const Ph &ph, TStage &ws, uint32_t &nf,
                                               uint32_t &ns, uint32_t &nx, uint32_t &nrec, uint32_t &far_min,
                                               bool all) {
     const uint32_t lane = lane_id();
@@ -208,9 +218,9 @@ __device__ __forceinline__ void team_classify(const Team &t, const TeamShared &s
         uint32_t v = 0;
         if (idx < nrec) {
             v = ws.iv[idx];
-            on_improved<DT>(t, s, v, ws.ik[idx], p, far_min);
+            on_improved<DT>(t, ph, v, ws.ik[idx], p, far_min);
         }
-        stage_push(s.ph, ws, nf, ns, nx, p, v);
+        stage_push(ph, ws, nf, ns, nx, p, v);
         start += 32u;
     }
     const uint32_t rest = nrec > start ? nrec - start : 0u;
@@ -223,15 +233,24 @@ __device__ __forceinline__ void team_classify(const Team &t, const TeamShared &s
     nrec = rest;
 }
 
+// The calling warp's index within its team and the team's warp count (a team
+// is the cluster of blocks that solves one instance; read from special registers).
+__device__ __forceinline__ uint32_t team_warp() {
+    return (cg::this_cluster().block_rank() * blockDim.x + threadIdx.x) >> 5;
+}
+__device__ __forceinline__ uint32_t team_warps() { return (cg::this_cluster().num_blocks() * blockDim.x) >> 5; }
+__device__ __forceinline__ uint32_t team_thread() { return cg::this_cluster().block_rank() * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ uint32_t team_threads() { return cg::this_cluster().num_blocks() * blockDim.x; }
+
 // LIGHT / HEAVY: relax the arcs of one list, split evenly over the team's warps
 // (merge-path over the entries' arc offsets; 32-entry window per warp).
 template <int DT, bool LIGHT, bool TAPE>
-__device__ void team_relax(const Team &t, const TeamShared &s, const uint2 *list, uint32_t count, uint32_t E,
-                           TStage &ws, int *sl, uint32_t &far_min, unsigned long long &improved,
-                           unsigned long long &relaxed) {
-    const Ph &ph = s.ph;
+__device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uint32_t &far_min,
+                           unsigned long long &improved, unsigned long long &relaxed) {
+    const uint32_t gw = team_warp(), nw_all = team_warps();
+    const uint2 *list = ph.in;
+    const uint32_t count = ph.count, E = ph.arcs;
     const uint32_t lane = lane_id();
-    const uint32_t gw = threadIdx.x >> 5, nw_all = blockDim.x >> 5;
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[2 * j]
     uint32_t nf = 0, ns = 0, nx = 0, nrec = 0;
     // merge-path over entries and arcs together (an entry weighs kTEntryCost arcs);
@@ -292,7 +311,7 @@ __device__ void team_relax(const Team &t, const TeamShared &s, const uint2 *list
             wend = (j + 32u < count) ? __ldcg(offs + 2ull * (j + 32u)) : E;
         };
         load_window(jw);
-        int *own_map = sl + gw * 32;
+        int *own_map = sl + (threadIdx.x >> 5) * 32;
         for (uint32_t base0 = e0; base0 < e1; base0 += 32u * kTIlp) {
             uint32_t ai[kTIlp], ov[kTIlp], okey[kTIlp];
             bool ok[kTIlp];
@@ -369,40 +388,40 @@ __device__ void team_relax(const Team &t, const TeamShared &s, const uint2 *list
             }
             if (nrec >= 32u) {
                 __syncwarp();
-                team_classify<DT>(t, s, ws, nf, ns, nx, nrec, far_min, false);
+                team_classify<DT>(t, ph, ws, nf, ns, nx, nrec, far_min, false);
             }
         }
         if (lane == 0) relaxed += e1 - e0;
     }
     if (nrec) {
         __syncwarp();
-        team_classify<DT>(t, s, ws, nf, ns, nx, nrec, far_min, true);
+        team_classify<DT>(t, ph, ws, nf, ns, nx, nrec, far_min, true);
     }
     drain_push(ph, ws, nf, ns, nx);
 }
 
 // SELECT: one pass over the far list with the new bucket's bounds [T_lo, T).
 template <int DT>
-__device__ void team_select(const Team &t, const TeamShared &s, const uint32_t *xin, uint32_t count, TStage &ws,
-                            uint32_t &next_min) {
-    const Ph &ph = s.ph;
+__device__ void team_select(const Team &t, const Ph &ph, TStage &ws, uint32_t &next_min) {
+    const uint32_t gw = team_warp(), nw = team_warps();
+    const uint32_t *xin = ph.xin;
+    const uint32_t count = ph.count;
     const uint32_t lane = lane_id();
-    const uint32_t gw = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint32_t nf = 0, ns = 0, nx = 0;
     for (uint32_t base = gw * 32u; base < count; base += nw * 32u) {
         const uint32_t idx = base + lane;
         TPush p{};
         uint32_t v = NONE;
-        if (idx < count && (v = __ldcs(xin + idx)) < t.n) {
+        if (idx < count && (v = __ldcg(xin + idx)) < t.n) {          // written by other blocks of the team
             const uint32_t k = (uint32_t)(__ldcg(t.packed + v) >> 32);
             if (k < ph.T_lo) {
-                s.fflag[v] = 0u;                     // its bucket was processed
+                ph.fflag[v] = 0u;                    // its bucket was processed
             } else if (k < ph.T) {
-                s.fflag[v] = 0u;                     // B_i of the new bucket: F and S
+                ph.fflag[v] = 0u;                    // B_i of the new bucket: F and S
                 const uint4 vi = t.vinfo[v];
                 p.fdeg = vi.y - vi.x;
                 p.f = p.fdeg != 0u;
-                s.sstamp[v] = ph.sst;
+                ph.sstamp[v] = ph.sst;
                 p.sdeg = vi.z - vi.y;
                 p.s = p.sdeg != 0u;
             } else {
@@ -479,65 +498,105 @@ __device__ __noinline__ void team_decide(TeamShared &s, const BGraphDev &g, cons
     }
 }
 
-// Destinations of the next phase's pushes (thread 0, after team_decide).
+// A block's view of the next phase (its thread 0, after the leader's
+// team_decide): lists from the team's slice of working memory, counters and
+// control from the leader's shared memory L.
 template <int DT>
-__device__ __noinline__ void set_phase(TeamShared &s, const BatchArgs &a, size_t off) {
-    const uint32_t mode = s.mode, cur = s.cur, scur = s.scur, xcur = s.xcur;
-    Ph &ph = s.ph;
+__device__ __noinline__ void build_view(Ph &ph, TeamShared *L, const BatchArgs &a, size_t off) {
+    const uint32_t mode = L->mode, cur = L->cur, scur = L->scur, xcur = L->xcur;
+    ph.mode = mode;
     ph.Fo = (cur ? a.ws.F0 : a.ws.F1) + off;                 // F[cur ^ 1]
-    ph.cF = &s.ctrF[cur ^ 1u];
+    ph.cF = &L->ctrF[cur ^ 1u];
     const uint32_t sp = mode == T_HEAVY ? scur ^ 1u : scur;  // a heavy pass feeds the next S
     ph.So = (sp ? a.ws.S1 : a.ws.S0) + off;
-    ph.cS = &s.ctrS[sp];
+    ph.cS = &L->ctrS[sp];
     const uint32_t xp = mode == T_SELECT ? xcur ^ 1u : xcur; // SELECT rebuilds the far list
     ph.Xo = (xp ? a.ws.X1 : a.ws.X0) + off;
-    ph.cX = &s.nX[xp];
-    ph.T = s.T;
-    ph.T_lo = s.T_lo;
-    ph.pstamp = s.pstamp;
-    ph.sst = s.sst;
-    ph.fst = s.fst;
+    ph.cX = &L->nX[xp];
+    unsigned long long c = 0ull;
+    if (mode == T_LIGHT) {
+        ph.in = (cur ? a.ws.F1 : a.ws.F0) + off;
+        c = L->ctrF[cur];
+    } else if (mode == T_HEAVY) {
+        ph.in = (scur ? a.ws.S1 : a.ws.S0) + off;
+        c = L->ctrS[scur];
+    } else {
+        ph.in = nullptr;
+        c = (unsigned long long)L->nX[xcur] << 32;
+    }
+    ph.xin = (xcur ? a.ws.X1 : a.ws.X0) + off;
+    ph.count = (uint32_t)(c >> 32);
+    ph.arcs = (uint32_t)c;
+    ph.nstamp = a.ws.nstamp + off;
+    ph.sstamp = a.ws.sstamp + off;
+    ph.fflag = a.ws.fflag + off;
+    ph.far_min = &L->far_min;
+    ph.next_min = &L->next_min;
+    ph.improve = &L->improve;
+    ph.a_light = &L->a_light;
+    ph.a_heavy = &L->a_heavy;
+    ph.T = L->T;
+    ph.T_lo = L->T_lo;
+    ph.pstamp = L->pstamp;
+    ph.sst = L->sst;
+    ph.fst = L->fst;
 }
 
 template <int DT, bool TAPE>
 __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
     __shared__ TeamShared s;
+    __shared__ Ph ph;
     __shared__ TStage stage[kTeamWarps];
     __shared__ int own_map[kTeamWarps * 32];
+    // A team is a cluster of blocks (one block when launched without clusters);
+    // block 0 of the cluster (the leader) holds the team's control and counters.
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t rank = cl.block_rank(), csize = cl.num_blocks();
+    const bool leader = rank == 0u;
     const uint32_t tid = threadIdx.x;
-    const size_t off = (size_t)blockIdx.x * a.cap;
+    const uint32_t team = blockIdx.x / csize;
+    const size_t off = (size_t)team * a.cap;
     Team t;
     t.packed = a.ws.packed + off;
-    if (tid == 0) {
-        s.gen = a.gen[blockIdx.x];
+    if (leader && tid == 0) {
+        s.gen = a.gen[team];
         s.nstamp = a.ws.nstamp + off;
         s.sstamp = a.ws.sstamp + off;
         s.fflag = a.ws.fflag + off;
     }
     for (;;) {
-        if (tid == 0) s.inst = atomicAdd(a.queue, 1u);
-        __syncthreads();
+        if (leader && tid == 0) s.inst = atomicAdd(a.queue, 1u);
+        cl.sync();
+        if (tid == 0) {
+            const TeamShared *L = cl.map_shared_rank(&s, 0);
+            s.inst = L->inst;
+            s.gen_seen = L->gen;
+            if (s.inst < a.n_inst) {
+                s.I = a.inst[s.inst];
+                s.G = a.graphs[s.I.graph];
+            }
+        }
+        cl.sync();                              // every block has its copy before the leader moves on
         const uint32_t ii = s.inst;
         if (ii >= a.n_inst) break;
-        if (tid == 0) {
-            s.I = a.inst[ii];
-            s.G = a.graphs[s.I.graph];
-        }
-        __syncthreads();
         t.vinfo = s.G.vinfo;
         t.arcs = s.G.arcs;
         t.n = s.G.n;
         t.m = s.G.m;
-        // stamps restart from 1 before the generator could wrap
-        if (s.gen > 0xF0000000u) {
-            for (size_t v = tid; v < a.cap; v += blockDim.x) { s.nstamp[v] = 0u; s.sstamp[v] = 0u; s.fflag[v] = 0u; }
-            __syncthreads();
-            if (tid == 0) s.gen = 1u;
+        // stamps restart from 1 before the leader's generator could wrap
+        if (s.gen_seen > 0xF0000000u) {
+            for (size_t v = team_thread(); v < a.cap; v += team_threads()) {
+                a.ws.nstamp[off + v] = 0u;
+                a.ws.sstamp[off + v] = 0u;
+                a.ws.fflag[off + v] = 0u;
+            }
+            cl.sync();
+            if (leader && tid == 0) s.gen = 1u;
         }
         const unsigned long long init = ((unsigned long long)inf_key<DT>() << 32) | NONE;
-        for (uint32_t v = tid; v < t.n; v += blockDim.x) t.packed[v] = init;
-        __syncthreads();
-        if (tid == 0) {
+        for (uint32_t v = team_thread(); v < t.n; v += team_threads()) t.packed[v] = init;
+        cl.sync();
+        if (leader && tid == 0) {
             s.t0 = wu::globaltimer();
             s.ctrF[0] = s.ctrF[1] = s.ctrS[0] = s.ctrS[1] = 0ull;
             s.a_light = s.a_heavy = s.improve = s.far_scanned = 0ull;
@@ -567,39 +626,36 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             s.mode = (s.ctrF[0] >> 32) ? T_LIGHT : ((s.ctrS[0] >> 32) ? T_HEAVY : T_DONE);
             if (s.mode == T_HEAVY) s.sst = ++s.gen;
         }
-        __syncthreads();
-        if (tid == 0) set_phase<DT>(s, a, off);
+        cl.sync();
+        if (tid == 0) build_view<DT>(ph, cl.map_shared_rank(&s, 0), a, off);
         __syncthreads();
         for (;;) {
-            const uint32_t mode = s.mode;
+            const uint32_t mode = ph.mode;
             if (mode == T_DONE) break;
             uint32_t fmin = inf_key<DT>();
             unsigned long long improved = 0, relaxed = 0;
             TStage &ws = stage[tid >> 5];
             if (mode == T_LIGHT) {
-                const unsigned long long c = s.ctrF[s.cur];
-                team_relax<DT, true, TAPE>(t, s, (s.cur ? a.ws.F1 : a.ws.F0) + off, (uint32_t)(c >> 32), (uint32_t)c,
-                                           ws, own_map, fmin, improved, relaxed);
+                team_relax<DT, true, TAPE>(t, ph, ws, own_map, fmin, improved, relaxed);
             } else if (mode == T_HEAVY) {
-                const unsigned long long c = s.ctrS[s.scur];
-                team_relax<DT, false, TAPE>(t, s, (s.scur ? a.ws.S1 : a.ws.S0) + off, (uint32_t)(c >> 32),
-                                            (uint32_t)c, ws, own_map, fmin, improved, relaxed);
+                team_relax<DT, false, TAPE>(t, ph, ws, own_map, fmin, improved, relaxed);
             } else {
-                team_select<DT>(t, s, (s.xcur ? a.ws.X1 : a.ws.X0) + off, s.nX[s.xcur], ws, fmin);
+                team_select<DT>(t, ph, ws, fmin);
             }
             fmin = warp_min(fmin);
             improved = warp_sum(improved);
             if (lane_id() == 0) {
-                if (fmin < inf_key<DT>()) atomicMin(mode == T_SELECT ? &s.next_min : &s.far_min, fmin);
-                if (improved) atomicAdd(&s.improve, improved);
-                if (relaxed) atomicAdd(mode == T_LIGHT ? &s.a_light : &s.a_heavy, relaxed);
+                if (fmin < inf_key<DT>()) atomicMin(mode == T_SELECT ? ph.next_min : ph.far_min, fmin);
+                if (improved) atomicAdd(ph.improve, improved);
+                if (relaxed) atomicAdd(mode == T_LIGHT ? ph.a_light : ph.a_heavy, relaxed);
             }
-            __syncthreads();
-            if (tid == 0) {
+            cl.sync();
+            if (leader && tid == 0) {
                 if (mode == T_SELECT) s.far_scanned += s.nX[s.xcur];
                 team_decide<DT>(s, s.G, a);
-                set_phase<DT>(s, a, off);
             }
+            cl.sync();
+            if (tid == 0) build_view<DT>(ph, cl.map_shared_rank(&s, 0), a, off);
             __syncthreads();
         }
         // unpack: dist = key bits; pred from the low word (tape: via the arc's row)
@@ -608,7 +664,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             const BGraphDev &G = s.G;
             const uint32_t src = I.src;
             uint32_t *dist = reinterpret_cast<uint32_t *>(I.dist);
-            for (uint32_t v = tid; v < t.n; v += blockDim.x) {
+            for (uint32_t v = team_thread(); v < t.n; v += team_threads()) {
                 const unsigned long long p = __ldcg(t.packed + v);
                 const uint32_t key = (uint32_t)(p >> 32), low = (uint32_t)p;
                 const bool reached = key < inf_key<DT>();
@@ -626,7 +682,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
                 }
             }
         }
-        if (tid == 0) {
+        if (leader && tid == 0) {
             long long *st = a.stats + (size_t)s.I.orig * kBStats;
             st[BS_BUCKETS] = s.buckets;
             st[BS_LIGHT] = s.n_light;
@@ -637,13 +693,13 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             st[BS_IMPROVE] = (long long)s.improve;
             st[BS_FARSCAN] = (long long)s.far_scanned;
             st[BS_NS] = (long long)(wu::globaltimer() - s.t0);
-            st[BS_TEAM] = blockIdx.x;
+            st[BS_TEAM] = team;
             st[BS_VLIGHT] = s.v_light;
             st[BS_VHEAVY] = s.v_heavy;
         }
-        __syncthreads();
+        cl.sync();
     }
-    if (tid == 0) a.gen[blockIdx.x] = s.gen;
+    if (leader && tid == 0) a.gen[team] = s.gen;
 }
 
 // ---------------------------------------------------------------------------
@@ -761,6 +817,7 @@ struct dsssp_batch {
     std::vector<Split *> splits;
     std::vector<uint32_t> m_of;
     uint32_t teams = 0;
+    uint32_t csize = 1;                     // blocks per team (cluster size)
     unsigned long long cap = 0;
     void *mem = nullptr;                    // one device allocation for everything below
     BGraphDev *d_graphs = nullptr;
@@ -818,6 +875,7 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
         if (opt->grid_size < 0 || opt->max_phases < 0) return DSSSP_ERR_INVALID_ARG;
         if (opt->grid_size) o.grid_size = opt->grid_size;
         if (opt->max_phases) o.max_phases = opt->max_phases;
+        o.team_blocks = opt->team_blocks;
     }
     const int dtype = graphs[0] ? graphs[0]->dtype : -1;
     const int device = graphs[0] ? graphs[0]->device : -1;
@@ -856,15 +914,39 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
         sp->pins++;
         b->splits[i] = sp;
     }
-    // teams: resident blocks, no more than instances, working memory within half of what is free
+    // team size (blocks per instance): a cluster when instances are fewer than the blocks
     int bps = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &bps, dtype == DSSSP_F32 ? (tape ? (const void *)k_batch<DSSSP_F32, true> : (const void *)k_batch<DSSSP_F32, false>)
-                                 : (const void *)k_batch<DSSSP_I32, false>,
-        kTeamThreads, 0);
+    const void *kfn = dtype == DSSSP_F32 ? (tape ? (const void *)k_batch<DSSSP_F32, true>
+                                                 : (const void *)k_batch<DSSSP_F32, false>)
+                                          : (const void *)k_batch<DSSSP_I32, false>;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn, kTeamThreads, 0);
     if (e != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
         return fail(DSSSP_ERR_CUDA);
     if (bps < 1) return fail(DSSSP_ERR_UNSUPPORTED);
+    const long long blocks_max = (long long)bps * sms;
+    int csize = o.team_blocks;
+    if (csize != 0 && csize != 1 && csize != 2 && csize != 4 && csize != 8) return fail(DSSSP_ERR_INVALID_ARG);
+    if (csize == 0) {            // the largest team with at most two instances per block on the GPU
+        csize = 1;
+        while (csize < 8 && (long long)n_inst * csize <= blocks_max) csize *= 2;
+    }
+    long long max_teams = blocks_max / csize;
+    if (csize > 1) {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = (unsigned)csize;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(csize * max_teams));
+        cfg.blockDim = dim3(kTeamThreads);
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if ((e = cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg)) != cudaSuccess) return fail(cuda_status(e));
+        if (clusters < 1) return fail(DSSSP_ERR_UNSUPPORTED);
+        max_teams = clusters;
+    }
     unsigned long long cap = 1;
     size_t sum_m = 0, sum_n_inst = 0;
     b->m_of.resize(n_graphs);
@@ -875,13 +957,14 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
     }
     for (int32_t k = 0; k < n_inst; ++k) sum_n_inst += (size_t)graphs[src_graph ? src_graph[k] : 0]->n;
     const size_t per_team = (size_t)cap * (8 + 4 + 4 + 4 + 8 * 4 + 4 * 2);
-    long long teams = (long long)bps * sms;
-    if (o.grid_size) teams = std::min<long long>(teams, o.grid_size);
+    long long teams = max_teams;
+    if (o.grid_size) teams = std::min<long long>(teams, std::max(1, o.grid_size / csize));
     teams = std::min<long long>(teams, n_inst);
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && per_team > 0)
         teams = std::max<long long>(1, std::min<long long>(teams, (long long)((free_b / 2) / per_team)));
     b->teams = (uint32_t)teams;
+    b->csize = (uint32_t)csize;
     b->cap = cap;
     // one allocation: tables, counters, per-team memory, tape
     size_t bytes = 0;
@@ -1031,13 +1114,19 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
     if (e == cudaSuccess) {
         void *kargs[] = {&b->args};
         cudaKernelNodeParams kp{};
-        kp.func = dtype == DSSSP_F32 ? (tape ? (void *)k_batch<DSSSP_F32, true> : (void *)k_batch<DSSSP_F32, false>)
-                                     : (void *)k_batch<DSSSP_I32, false>;
-        kp.gridDim = dim3(b->teams);
+        kp.func = const_cast<void *>(kfn);
+        kp.gridDim = dim3(b->teams * b->csize);
         kp.blockDim = dim3(kTeamThreads);
         kp.sharedMemBytes = 0;
         kp.kernelParams = kargs;
         e = cudaGraphAddKernelNode(&n_kernel, b->graph, &n_memset, 1, &kp);
+    }
+    if (e == cudaSuccess && b->csize > 1) {
+        cudaKernelNodeAttrValue v{};
+        v.clusterDim.x = b->csize;
+        v.clusterDim.y = 1;
+        v.clusterDim.z = 1;
+        e = cudaGraphKernelNodeSetAttribute(n_kernel, cudaKernelNodeAttributeClusterDimension, &v);
     }
     if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
     if (e != cudaSuccess) {

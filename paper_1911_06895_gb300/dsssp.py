@@ -54,7 +54,7 @@ class dsssp_options(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("mode", ctypes.c_int32),
                 ("block_size", ctypes.c_int32), ("grid_size", ctypes.c_int32), ("solo_work", ctypes.c_int32),
                 ("max_phases", ctypes.c_int64), ("timeout_ns", ctypes.c_int64), ("test_hook", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 5)]
+                ("team_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 class dsssp_stats(ctypes.Structure):

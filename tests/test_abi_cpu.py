@@ -76,7 +76,8 @@ def test_struct_layout_matches_header():
              offsetof(dsssp_options, max_phases), offsetof(dsssp_options, test_hook),
              offsetof(dsssp_stats, block_size), sizeof(dsssp_batch_stats),
              offsetof(dsssp_batch_stats, team));
-      printf("%zu %zu\n", sizeof(dsssp_tune_options), offsetof(dsssp_tune_options, candidates));
+      printf("%zu %zu %zu\n", sizeof(dsssp_tune_options), offsetof(dsssp_tune_options, candidates),
+             offsetof(dsssp_options, team_blocks));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -89,5 +90,5 @@ def test_struct_layout_matches_header():
             ds.dsssp_options.max_phases.offset, ds.dsssp_options.test_hook.offset,
             ds.dsssp_stats.block_size.offset, ctypes.sizeof(ds.dsssp_batch_stats),
             ds.dsssp_batch_stats.team.offset, ctypes.sizeof(ds.dsssp_tune_options),
-            ds.dsssp_tune_options.candidates.offset]
+            ds.dsssp_tune_options.candidates.offset, ds.dsssp_options.team_blocks.offset]
     assert [int(x) for x in out] == want

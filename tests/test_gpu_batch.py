@@ -98,6 +98,49 @@ def test_one_team_reuses_its_memory(ds):
     b.close()
 
 
+@pytest.mark.parametrize("team_blocks", [1, 2, 4, 8])
+def test_cluster_teams(ds, team_blocks):
+    """An instance solved by a cluster of blocks sharing its control through distributed
+    shared memory gives the same bits; few teams force several instances per team."""
+    g, sources, _ = W.rmat22_unit(scale=15, n_sources=10)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for opt in (dict(team_blocks=team_blocks), dict(team_blocks=team_blocks, grid_size=2 * team_blocks)):
+        for delta in (0.03, 0.3):
+            b = batch(ds, h, [delta], sources, **opt)
+            for rep in range(2):
+                b.run()
+                st = b.sync(stats=True)
+                ds_, ps_ = fetch(b)
+                for k, s in enumerate(sources):
+                    same(ds_[k], ps_[k], refd[k], refp[k], f"{opt} delta {delta} rep {rep} src {s}")
+            if "grid_size" in opt:
+                assert max(x["team"] for x in st) <= 1
+            b.close()
+
+
+def test_cluster_teams_tape_and_graphs(ds):
+    g, sources, _ = W.rmat20_lognormal(scale=13, n_sources=6)
+    cs = [graphgen.random_costs(g.n, 70 + k) for k in range(len(sources))]
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [0.7], sources, tape=True, team_blocks=4)
+    b.run()
+    b.sync()
+    ref = oracle.tree_gradient_many(g.row_ptr, g.col, g.w, sources, 0.7, cs)
+    assert_grad_close(gpu_grad(ds, b, cs, g.m), ref, "cluster tape")
+    b.close()
+    fam = W.er_family(count=10, n_lo=200, n_hi=30000)
+    hs = [ds.Graph(x.row_ptr, x.col, x.w) for x, _ in fam]
+    b = batch(ds, hs, [0.2] * len(fam), [s for _, s in fam], src_graph=list(range(len(fam))), team_blocks=2)
+    b.run()
+    b.sync()
+    ds_, ps_ = fetch(b)
+    for k, (x, s) in enumerate(fam):
+        d_ref, p_ref = oracle.dijkstra(x.row_ptr, x.col, x.w, s)
+        same(ds_[k], ps_[k], d_ref, p_ref, f"graph {k}")
+    b.close()
+
+
 def edge_graphs():
     out = []
     out.append((graphgen.from_arcs(1, [], np.zeros(0, np.float32), dtype=np.float32), 0, 1.0))
