@@ -339,6 +339,20 @@ def main():
         achieved = tot_bytes / (tot_ms * 1e-3) / 1e9
         light_gbs = tot_light_b / (tot_light_ns * 1e-9) / 1e9 if tot_light_ns else None
 
+    # the same 64 sources per Delta as one batch (one launch, a cluster of blocks per source)
+    batched_same = None
+    if world == 1 and not args.no_extras:
+        batched_same = {}
+        for d in deltas:
+            tb, _ = ds.tune_team_blocks(h, [d], srcs)
+            b = ds.Batch(h, [d], srcs, options=ds.make_options(team_blocks=tb))
+            ms_b = _events_ms(torch, b.run, 2)
+            b.sync()
+            b.close()
+            batched_same[str(d)] = {"team_blocks": tb, "ms": ms_b, "gteps": g.m * len(srcs) / (ms_b * 1e-3) / 1e9,
+                                    "one_by_one_gteps": per_delta[str(d)]["gteps"],
+                                    "speedup": per_delta[str(d)]["ms_per_solve"] * len(srcs) / ms_b}
+
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args)
@@ -378,6 +392,10 @@ def main():
             "gpu_launches": 4 * solves * args.steps,
         }
         line.update(extras)
+        if batched_same is not None:
+            line["batched_same_workload"] = {
+                "note": "the same 64 sources per Delta solved as one batch instead of one after another",
+                "per_delta": batched_same}
         print(json.dumps(line), flush=True)
     if dist_pg:
         dist_pg.barrier()
@@ -421,8 +439,9 @@ def run_extras(ds, torch):
     t = time.perf_counter()
     (d_b,), _ = ds.autotune(h, [srcs[:8]], target="batch")
     (d_p,), _ = ds.autotune(h, [srcs[:4]], target="solve")
+    tb_a, _ = ds.tune_team_blocks(h, [d_b], srcs)
     tune_s = time.perf_counter() - t
-    b = ds.Batch(h, [d_b], srcs)
+    b = ds.Batch(h, [d_b], srcs, options=ds.make_options(team_blocks=tb_a))
     ms_b = _events_ms(torch, b.run, 3)
     bst = b.sync(stats=True)
     b.close()
@@ -436,7 +455,7 @@ def run_extras(ds, torch):
     h.sync()
     h.close()
     out["batched"]["rmat20_unit_256src"] = {
-        "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "ms": ms_b,
+        "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "team_blocks": tb_a, "ms": ms_b,
         "gteps": g.m * len(srcs) / (ms_b * 1e-3) / 1e9, "plain_delta": d_p, "plain_ms": ms_p,
         "plain_gteps": g.m * len(srcs) / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s,
         "algorithmic_gbs": gbs_a, "hbm_frac": gbs_a / peak}
@@ -448,8 +467,9 @@ def run_extras(ds, torch):
     msum = sum(x.m for x, _ in fam)
     t = time.perf_counter()
     deltas, _ = ds.autotune(hs, [[s] for s in fsrc], target="batch", refine=1)
+    tb_b, _ = ds.tune_team_blocks(hs, deltas, fsrc, src_graph=list(range(len(fam))))
     tune_s = time.perf_counter() - t
-    b = ds.Batch(hs, deltas, fsrc, src_graph=list(range(len(fam))))
+    b = ds.Batch(hs, deltas, fsrc, src_graph=list(range(len(fam))), options=ds.make_options(team_blocks=tb_b))
     ms_b = _events_ms(torch, b.run, 3)
     bst = b.sync(stats=True)
     b.close()
@@ -465,7 +485,7 @@ def run_extras(ds, torch):
         hh.sync()
         hh.close()
     out["batched"]["er512"] = {
-        "graphs": len(fam), "sum_n": sum(x.n for x, _ in fam), "sum_m": msum,
+        "graphs": len(fam), "sum_n": sum(x.n for x, _ in fam), "sum_m": msum, "team_blocks": tb_b,
         "delta_range": [min(deltas), max(deltas)], "ms": ms_b, "gteps": msum / (ms_b * 1e-3) / 1e9,
         "plain_ms": ms_p, "plain_gteps": msum / (ms_p * 1e-3) / 1e9, "speedup": ms_p / ms_b, "tune_s": tune_s,
         "algorithmic_gbs": gbs_b, "hbm_frac": gbs_b / peak}
@@ -475,11 +495,13 @@ def run_extras(ds, torch):
     h = ds.Graph(g.row_ptr, g.col, g.w)
     t = time.perf_counter()
     (d_b,), _ = ds.autotune(h, [srcs[:8]], target="batch")
+    tb_c, _ = ds.tune_team_blocks(h, [d_b], srcs)
     tune_s = time.perf_counter() - t
     cs = [torch.from_numpy(c).cuda()] * len(srcs)
     gw = torch.empty(g.m, dtype=torch.float32, device="cuda")
-    bt = ds.Batch(h, [d_b], srcs, tape=True)
-    bn = ds.Batch(h, [d_b], srcs)
+    opt_c = ds.make_options(team_blocks=tb_c)
+    bt = ds.Batch(h, [d_b], srcs, tape=True, options=opt_c)
+    bn = ds.Batch(h, [d_b], srcs, options=opt_c)
 
     def fwd_bwd():
         bt.run()
@@ -500,7 +522,8 @@ def run_extras(ds, torch):
     h.close()
     sm = g.m * len(srcs)
     out["fwd_bwd"]["rmat20_lognormal_32src"] = {
-        "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "fwd_bwd_ms": ms_fb, "fwd_ms": ms_f,
+        "n": g.n, "m": g.m, "instances": len(srcs), "delta": d_b, "team_blocks": tb_c, "fwd_bwd_ms": ms_fb,
+        "fwd_ms": ms_f,
         "bwd_ms": ms_bw, "fwd_bwd_gteps": sm / (ms_fb * 1e-3) / 1e9, "fwd_gteps": sm / (ms_f * 1e-3) / 1e9,
         "plain_solve_ms": ms_p, "plain_solve_gteps": sm / (ms_p * 1e-3) / 1e9,
         "fwd_bwd_over_fwd": ms_fb / ms_f, "tune_s": tune_s}

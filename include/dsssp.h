@@ -338,6 +338,16 @@ typedef struct {
 dsssp_status dsssp_autotune(dsssp_graph *const *graphs, int32_t n_graphs, const int32_t *sample_src, int32_t k,
                             const dsssp_tune_options *opt, double *delta_out, double *ms_out, void *stream);
 
+/* Choose the team size of a batch (dsssp_options.team_blocks: blocks per instance, 1, 2, 4 or
+ * 8) by timing the whole batch at each size: builds the plan the arguments describe (as
+ * dsssp_batch_create, outputs written) once per size, runs it twice and keeps the fastest
+ * second run. team_blocks_out receives the size; ms_out (may be NULL) its device time.
+ * Waits for its work. Errors: those of dsssp_batch_create / run / sync. */
+dsssp_status dsssp_tune_team_blocks(dsssp_graph *const *graphs, int32_t n_graphs, const double *delta,
+                                    int32_t n_inst, const int32_t *src, const int32_t *src_graph,
+                                    void *const *dist, int32_t *const *pred, int32_t *team_blocks_out,
+                                    double *ms_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -719,41 +719,52 @@ struct BwdArgs {
 };
 
 __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
-    __shared__ uint32_t s_inst, s_n[2], s_reached, s_done;
+    // a team (cluster of blocks, as in the forward launch) per instance; the
+    // ready-list counters live in the leader block's shared memory
+    struct BwdShared {
+        uint32_t inst, n[2], reached, done;
+    };
+    __shared__ BwdShared bs;
+    cg::cluster_group cl = cg::this_cluster();
+    const bool leader = cl.block_rank() == 0u;
+    BwdShared *Ls = cl.map_shared_rank(&bs, 0);
     const uint32_t tid = threadIdx.x;
-    const size_t off = (size_t)blockIdx.x * a.cap;
+    const uint32_t tt = team_thread(), nt = team_threads();
+    const size_t off = (size_t)(blockIdx.x / cl.num_blocks()) * a.cap;
     double *acc = reinterpret_cast<double *>(a.ws.packed + off);     // subtree sums
     uint32_t *L[2] = {reinterpret_cast<uint32_t *>(a.ws.F0 + off), reinterpret_cast<uint32_t *>(a.ws.F0 + off) + a.cap};
     uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws.F1 + off);     // children not yet summed
     for (;;) {
-        if (tid == 0) s_inst = atomicAdd(a.queue, 1u);
-        __syncthreads();
-        const uint32_t ii = s_inst;
+        if (leader && tid == 0) bs.inst = atomicAdd(a.queue, 1u);
+        cl.sync();
+        const uint32_t ii = Ls->inst;
+        cl.sync();                              // all have read it before the leader moves on
         if (ii >= a.n_inst) break;
         const BInstDev I = a.inst[ii];
         const uint32_t n = a.graphs[I.graph].n, m = a.graphs[I.graph].m;
         const float *c = a.c[I.orig];
         double *g64 = a.grad64[I.graph];
-        for (uint32_t v = tid; v < n; v += blockDim.x) { acc[v] = 0.0; cnt[v] = 0u; }
-        if (tid == 0) { s_n[0] = s_n[1] = 0u; s_reached = 0u; s_done = 0u; }
-        __syncthreads();
+        for (uint32_t v = tt; v < n; v += nt) { acc[v] = 0.0; cnt[v] = 0u; }
+        if (leader && tid == 0) { bs.n[0] = bs.n[1] = 0u; bs.reached = 0u; bs.done = 0u; }
+        cl.sync();
         uint32_t reached = 0;
-        for (uint32_t v = tid; v < n; v += blockDim.x) {
+        for (uint32_t v = tt; v < n; v += nt) {
             const uint32_t p = I.parent[v];
             if (p == NONE) continue;
             ++reached;
             if (v != I.src && p < n) atomicAdd(cnt + p, 1u);
         }
         reached = __reduce_add_sync(FULL, reached);
-        if (lane_id() == 0 && reached) atomicAdd(&s_reached, reached);
-        __syncthreads();
-        for (uint32_t v = tid; v < n; v += blockDim.x)       // leaves
-            if (I.parent[v] != NONE && __ldcg(cnt + v) == 0u) L[0][atomicAdd(&s_n[0], 1u)] = v;
-        __syncthreads();
+        if (lane_id() == 0 && reached) atomicAdd(&Ls->reached, reached);
+        cl.sync();
+        for (uint32_t v = tt; v < n; v += nt)                // leaves
+            if (I.parent[v] != NONE && __ldcg(cnt + v) == 0u) L[0][atomicAdd(&Ls->n[0], 1u)] = v;
+        cl.sync();
         uint32_t cur = 0, done = 0;
-        while (s_n[cur] != 0u) {
-            const uint32_t cnt_cur = s_n[cur];
-            for (uint32_t k = tid; k < cnt_cur; k += blockDim.x) {
+        for (;;) {
+            const uint32_t cnt_cur = Ls->n[cur];
+            if (cnt_cur == 0u) break;
+            for (uint32_t k = tt; k < cnt_cur; k += nt) {
                 const uint32_t v = __ldcg(L[cur] + k);
                 const double sum = __ldcg(acc + v) + (double)c[v];
                 ++done;
@@ -762,19 +773,19 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
                 if (e < m) atomicAdd(g64 + e, sum);
                 if (p < n) {
                     atomicAdd(acc + p, sum);
-                    if (atomicSub(cnt + p, 1u) == 1u) L[cur ^ 1u][atomicAdd(&s_n[cur ^ 1u], 1u)] = p;
+                    if (atomicSub(cnt + p, 1u) == 1u) L[cur ^ 1u][atomicAdd(&Ls->n[cur ^ 1u], 1u)] = p;
                 }
             }
-            __syncthreads();
-            if (tid == 0) s_n[cur] = 0u;
+            cl.sync();
+            if (leader && tid == 0) bs.n[cur] = 0u;
             cur ^= 1u;
-            __syncthreads();
+            cl.sync();
         }
         done = __reduce_add_sync(FULL, done);
-        if (lane_id() == 0 && done) atomicAdd(&s_done, done);
-        __syncthreads();
-        if (tid == 0 && s_done != s_reached) atomicCAS(a.err, 0, (int)DSSSP_ERR_DEGENERATE);   // a cycle
-        __syncthreads();
+        if (lane_id() == 0 && done) atomicAdd(&Ls->done, done);
+        cl.sync();
+        if (leader && tid == 0 && bs.done != bs.reached) atomicCAS(a.err, 0, (int)DSSSP_ERR_DEGENERATE);   // a cycle
+        cl.sync();
     }
 }
 
@@ -926,7 +937,7 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
     const long long blocks_max = (long long)bps * sms;
     int csize = o.team_blocks;
     if (csize != 0 && csize != 1 && csize != 2 && csize != 4 && csize != 8) return fail(DSSSP_ERR_INVALID_ARG);
-    if (csize == 0) {            // the largest team with at most two instances per block on the GPU
+    if (csize == 0) {            // largest power of two <= 8 with instances x team blocks <= 2 x resident blocks
         csize = 1;
         while (csize < 8 && (long long)n_inst * csize <= blocks_max) csize *= 2;
     }
@@ -1237,8 +1248,20 @@ dsssp_status dsssp_backward(dsssp_batch *b, const float *const *c, float *const 
     ba.grad64 = b->d_grad64_ptr;
     ba.ws = b->ws;
     ba.cap = b->cap;
-    k_backward<<<b->teams, kTeamThreads, 0, st>>>(ba);
-    DSSSP_TRY(cudaGetLastError());
+    {
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = b->csize;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.gridDim = dim3(b->teams * b->csize);
+        cfg.blockDim = dim3(kTeamThreads);
+        cfg.stream = st;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        DSSSP_TRY(cudaLaunchKernelEx(&cfg, k_backward, ba));
+    }
     if (max_m) {
         const dim3 grid((unsigned)std::min<uint32_t>(1024u, (max_m + 1023u) / 1024u), (unsigned)b->n_graphs);
         k_grad_out<<<grid, 256, 0, st>>>(b->d_grad64_ptr, b->d_gradw_ptr, b->d_m_of,

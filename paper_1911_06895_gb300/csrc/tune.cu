@@ -228,3 +228,50 @@ extern "C" dsssp_status dsssp_autotune(dsssp_graph *const *graphs, int32_t n_gra
     }
     return DSSSP_OK;
 }
+
+extern "C" dsssp_status dsssp_tune_team_blocks(dsssp_graph *const *graphs, int32_t n_graphs, const double *delta,
+                                               int32_t n_inst, const int32_t *src, const int32_t *src_graph,
+                                               void *const *dist, int32_t *const *pred, int32_t *team_blocks_out,
+                                               double *ms_out, void *stream) {
+    if (!team_blocks_out || !graphs || n_graphs < 1) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(graphs[0] ? graphs[0]->device : 0);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    DSSSP_TRY(cudaEventCreate(&e0));
+    DSSSP_TRY(cudaEventCreate(&e1));
+    double best_ms = std::numeric_limits<double>::infinity();
+    int32_t best = 0;
+    dsssp_status rc = DSSSP_OK;
+    for (int32_t tb : {1, 2, 4, 8}) {
+        dsssp_options o;
+        dsssp_options_default(&o);
+        o.team_blocks = tb;
+        dsssp_batch *b = nullptr;
+        rc = dsssp_batch_create(graphs, n_graphs, delta, n_inst, src, src_graph, dist, pred, 0u, &o, stream, &b);
+        if (rc == DSSSP_ERR_UNSUPPORTED) {      // this cluster size cannot be co-scheduled here
+            rc = DSSSP_OK;
+            continue;
+        }
+        if (rc != DSSSP_OK) break;
+        rc = dsssp_batch_run(b, stream);                                  // warm-up
+        if (rc == DSSSP_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = DSSSP_ERR_CUDA;
+        if (rc == DSSSP_OK) rc = dsssp_batch_run(b, stream);
+        if (rc == DSSSP_OK && cudaEventRecord(e1, st) != cudaSuccess) rc = DSSSP_ERR_CUDA;
+        if (rc == DSSSP_OK) rc = dsssp_batch_sync(b, nullptr, stream);
+        float t = 0.f;
+        if (rc == DSSSP_OK && cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) rc = DSSSP_ERR_CUDA;
+        dsssp_batch_destroy(b);
+        if (rc != DSSSP_OK) break;
+        if (t < best_ms) {
+            best_ms = t;
+            best = tb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != DSSSP_OK) return rc;
+    if (best == 0) return DSSSP_ERR_UNSUPPORTED;
+    *team_blocks_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return DSSSP_OK;
+}

@@ -122,11 +122,14 @@ dsssp_solve_batched = _fn("dsssp_solve_batched", ctypes.c_int,
 dsssp_backward = _fn("dsssp_backward", ctypes.c_int, [_vp, _vp, _vp, _u32, _vp])
 dsssp_autotune = _fn("dsssp_autotune", ctypes.c_int,
                      [_vp, _i32, _vp, _i32, ctypes.POINTER(dsssp_tune_options), _vp, _vp, _vp])
+dsssp_tune_team_blocks = _fn("dsssp_tune_team_blocks", ctypes.c_int,
+                             [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_i32),
+                              ctypes.POINTER(ctypes.c_double), _vp])
 
 EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create", "dsssp_graph_destroy",
             "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc",
             "dsssp_batch_create", "dsssp_batch_run", "dsssp_batch_sync", "dsssp_batch_destroy",
-            "dsssp_solve_batched", "dsssp_backward", "dsssp_autotune"]
+            "dsssp_solve_batched", "dsssp_backward", "dsssp_autotune", "dsssp_tune_team_blocks"]
 
 NOALLOC_MAX_VERTICES = 1 << 17
 
@@ -388,3 +391,22 @@ def autotune(graphs, sample_sources, target: str = "solve", candidates=None, ref
     check(dsssp_autotune(_ptr_array([g.handle.value for g in graphs]), len(graphs), flat, k, ctypes.byref(o),
                          dout, mout, _stream_ptr(stream)), "dsssp_autotune")
     return list(dout), list(mout)
+
+
+def tune_team_blocks(graphs, deltas, sources, src_graph=None, stream=None):
+    """Blocks per instance (1, 2, 4 or 8) at which this batch runs fastest; returns (team_blocks, ms)."""
+    import torch
+    graphs = list(graphs) if isinstance(graphs, (list, tuple)) else [graphs]
+    deltas = list(deltas) if isinstance(deltas, (list, tuple, np.ndarray)) else [deltas]
+    k = len(sources)
+    sg = [0] * k if src_graph is None else [int(g) for g in src_graph]
+    tdt = torch.float32 if graphs[0].dtype_code == DSSSP_F32 else torch.int32
+    dist = [torch.empty(graphs[g].n, dtype=tdt, device="cuda") for g in sg]
+    tb = _i32(0)
+    ms = ctypes.c_double(0.0)
+    check(dsssp_tune_team_blocks(_ptr_array([g.handle.value for g in graphs]), len(graphs),
+                                 (ctypes.c_double * len(deltas))(*[float(x) for x in deltas]), k,
+                                 (ctypes.c_int32 * k)(*[int(s) for s in sources]), (ctypes.c_int32 * k)(*sg),
+                                 _ptr_array([d.data_ptr() for d in dist]), None, ctypes.byref(tb), ctypes.byref(ms),
+                                 _stream_ptr(stream)), "dsssp_tune_team_blocks")
+    return int(tb.value), float(ms.value)

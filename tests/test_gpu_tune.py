@@ -68,3 +68,16 @@ def test_tune_rejects_bad_arguments(ds):
         ds.autotune(h, [g.n], target="solve")
     with pytest.raises(ds.DsssError):
         ds.autotune(h, srcs, target="solve", candidates=[-1.0])
+
+
+def test_tune_team_blocks(ds):
+    g, sources, _ = W.rmat22_unit(scale=15, n_sources=8)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    tb, ms = ds.tune_team_blocks(h, [0.1], sources)
+    assert tb in (1, 2, 4, 8) and ms > 0
+    b = ds.Batch(h, [0.1], sources, options=ds.make_options(team_blocks=tb))
+    b.run()
+    b.sync()
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, sources[0])
+    assert np.array_equal(b.dist[0].cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
+    b.close()
