@@ -74,6 +74,9 @@ typedef enum {
 /* dsssp_options.flags */
 #define DSSSP_FLAG_ASYNC 0x1u    /* do not wait for the solve: device-side status is kept in the
                                     graph and returned by dsssp_graph_sync()                        */
+#define DSSSP_FLAG_NO_FUSE 0x2u  /* keep every heavy pass in a phase of its own; by default, when
+                                    bucket i+1 already holds vertices, bucket i's heavy pass and
+                                    bucket i+1's first light round share one phase (same results)   */
 
 /* Test hooks (dsssp_options.test_hook): exercise error paths without a fault. */
 #define DSSSP_HOOK_NONE 0

@@ -316,6 +316,7 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     a.m = (uint32_t)g->m;
     // persistent mode only: the stepped mode has no grid barrier to save
     a.solo_work = (opt.mode == DSSSP_MODE_PERSISTENT && opt.solo_work > 0) ? (uint32_t)opt.solo_work : 0u;
+    a.fuse = (opt.flags & DSSSP_FLAG_NO_FUSE) ? 0u : 1u;
     a.src = (uint32_t)src;
     a.inf_key = key_inf(g->dtype);
     a.dtype = g->dtype;

@@ -100,7 +100,8 @@ enum Mode : uint32_t {
     MODE_LIGHT = 0,    // relax light arcs of the frontier  (t_Req = A_L^T (t o t_Bi))
     MODE_HEAVY = 1,    // relax heavy arcs of S             (t_Req = A_H^T (t o S))
     MODE_REBIN = 2,    // move overflow vertices into the bucket slots of a new window
-    MODE_DONE = 3
+    MODE_DONE = 3,
+    MODE_FUSED = 4     // the heavy pass of bucket i together with the first light round of bucket i+1
 };
 
 // Buckets. Section III-B's B_j are kept explicitly for a window of kSlots
@@ -141,7 +142,10 @@ struct alignas(64) PhaseDesc {
     uint32_t solo;          // 1: block 0 alone runs this phase (little work), the others wait
     uint32_t wbase32;       // first bucket of the slot window (low 32 bits, for slot stamps)
     uint32_t pad;
+    uint32_t count_h;       // FUSED: entries of the S list whose heavy arcs are relaxed
+    uint32_t arcs_h;        // FUSED: their heavy arcs
 };
+constexpr int kDescVec = (int)(sizeof(PhaseDesc) / 16);   // 16-byte words of a PhaseDesc
 
 // State only the serial step reads and writes.
 struct alignas(16) SerialState {
@@ -209,6 +213,7 @@ struct SolveArgs {
     uint32_t src;
     uint32_t inf_key;
     uint32_t solo_work;             // phases with at most this much work run solo
+    uint32_t fuse;                  // 1: heavy pass of bucket i fused with the first light round of i+1
     int32_t dtype;
     int32_t test_hook;
     uint32_t nblocks;

@@ -432,18 +432,18 @@ __device__ __forceinline__ void classify_records(const SolveArgs &a, const Block
 }
 
 // LIGHT / HEAVY: relax the arcs of a list, split evenly over the warps.
+// The list read is F (LIGHT), the slot `sl` of a bucket's first round (LIGHT,
+// sl < kNoSlot) or S (HEAVY); `count` entries holding `E` arcs.
 template <int DT, bool LIGHT>
 __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &acc, int *slot, WarpStage *stage,
-                           uint32_t gw, uint32_t nw_all) {
+                           uint32_t gw, uint32_t nw_all, uint32_t count, uint32_t E, uint32_t sl) {
     const PhaseDesc &d = bvw.d;
     const uint32_t lane = lane_id();
-    const bool from_slot = LIGHT && d.slot < kNoSlot;
-    const uint2 *list = LIGHT ? (from_slot ? a.SL + (size_t)d.slot * a.n : (d.cur ? a.F1 : a.F0))
+    const bool from_slot = LIGHT && sl < kNoSlot;
+    const uint2 *list = LIGHT ? (from_slot ? a.SL + (size_t)sl * a.n : (d.cur ? a.F1 : a.F0))
                               : (d.scur ? a.S1 : a.S0);
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[2 * j]
-    const uint32_t count = d.count;
-    const uint32_t E = d.arcs;
-    const uint32_t T_lo = d.T_lo;
+    const uint32_t T_lo = from_slot ? d.T_lo : 0u;          // only slot entries can be stale
     uint32_t ov_min = inf_key<DT>();
     uint32_t improved = 0, nrec = 0;
     PushCnt q{};
@@ -509,7 +509,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
                 const uint32_t k = (uint32_t)(__ldcg(a.packed + wv) >> 32);
                 const uint4 vi = a.vinfo[wv];
                 wbeg = LIGHT ? vi.x : vi.y;
-                wkey = k >= T_lo ? k : inf_key<DT>();
+                wkey = (T_lo == 0u || k >= T_lo) ? k : inf_key<DT>();
             } else {
                 wv = 0; woff = 0xFFFFFFFFu; wbeg = 0; wkey = inf_key<DT>();
             }
@@ -668,7 +668,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
     }
     PhaseDesc od;                                  // the phase that just ended
     #pragma unroll
-    for (int k = 0; k < 4; ++k)
+    for (int k = 0; k < kDescVec; ++k)
         reinterpret_cast<uint4 *>(&od)[k] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + k);
     unsigned long long ctrF[2] = {__ldcg(&c->ctrF[0]), __ldcg(&c->ctrF[1])};
     unsigned long long ctrS[2] = {__ldcg(&c->ctrS[0]), __ldcg(&c->ctrS[1])};
@@ -684,7 +684,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
     s.t_last = now;
     const uint32_t mode = s.mode;
     if (mode == MODE_LIGHT) s.st[ST_NSLIGHT] += (long long)dt;
-    else if (mode == MODE_HEAVY) s.st[ST_NSHEAVY] += (long long)dt;
+    else if (mode == MODE_HEAVY || mode == MODE_FUSED) s.st[ST_NSHEAVY] += (long long)dt;
     else if (mode == MODE_REBIN) s.st[ST_NSREBIN] += (long long)dt;
     s.phases += 1;
     PhaseDesc nd{};
@@ -715,6 +715,18 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
             s.scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
             s.sround += 1u;
             break;
+        case MODE_FUSED:                           // bucket i's S and bucket i+1's slot are consumed
+            s.st[ST_LIGHT] += 1;
+            s.st[ST_HEAVY] += 1;
+            s.st[ST_VLIGHT] += (long long)od.count;
+            s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
+            c->ctrSL[od.slot] = 0ull;
+            c->nSH[od.slot] = 0u;
+            c->ctrS[s.scur] = 0ull;
+            ctrS[s.scur] = 0ull;
+            s.scur ^= 1u;
+            s.sround += 1u;
+            break;
         case MODE_REBIN:
             s.st[ST_REBIN] += 1;
             c->nOV[s.ov_cur] = 0u;
@@ -735,9 +747,36 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
             nd.count = (uint32_t)(ctrF[nxt] >> 32);
             nd.arcs = (uint32_t)ctrF[nxt];
         } else if ((ctrS[s.scur] >> 32) != 0ull) { // bucket settled: heavy pass over S
-            next_mode = MODE_HEAVY;
-            nd.count = (uint32_t)(ctrS[s.scur] >> 32);
-            nd.arcs = (uint32_t)ctrS[s.scur];
+            // When bucket i+1 already holds vertices, its first light round runs in the
+            // same phase as bucket i's heavy pass: heavy weights exceed Delta, so the
+            // heavy pass only adds to buckets >= i+1, and what it adds to i+1 is relaxed
+            // in i+1's later rounds (the fixed point does not depend on the order).
+            const int j = (int)(s.bucket - s.wbase + 1);
+            unsigned long long jsl = 0ull;
+            uint32_t jsh = 0u, jlo = 0u, jhi = 0u;
+            if (a.fuse && j >= 0 && j < (int)kSlots) {
+                jsl = __ldcg(&c->ctrSL[j]);
+                jsh = __ldcg(&c->nSH[j]);
+                jlo = __ldcg(&c->thr[j]);
+                jhi = __ldcg(&c->thr[j + 1]);
+            }
+            if ((jsl >> 32) != 0ull || jsh != 0u) {
+                next_mode = MODE_FUSED;
+                s.bucket += 1;
+                s.st[ST_BUCKETS] += 1;
+                s.T_lo = jlo;
+                s.T = jhi;
+                nd.slot = (uint32_t)j;
+                nd.count = (uint32_t)(jsl >> 32);
+                nd.arcs = (uint32_t)jsl;
+                nd.count2 = jsh;
+                nd.count_h = (uint32_t)(ctrS[s.scur] >> 32);
+                nd.arcs_h = (uint32_t)ctrS[s.scur];
+            } else {
+                next_mode = MODE_HEAVY;
+                nd.count = (uint32_t)(ctrS[s.scur] >> 32);
+                nd.arcs = (uint32_t)ctrS[s.scur];
+            }
         } else {
             // next non-empty bucket of the window: slot counters read 8 at a time
             const int first = (int)(s.bucket - s.wbase + 1);   // slots before it are consumed
@@ -799,15 +838,17 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
     nd.cur = s.cur;
     nd.scur = s.scur;
     // S pushes: into the current S, except during a heavy pass, which feeds the next one
-    nd.spush = next_mode == MODE_HEAVY ? s.scur ^ 1u : s.scur;
-    nd.sstamp = next_mode == MODE_HEAVY ? s.sround + 1u : s.sround;
+    const bool heavy = next_mode == MODE_HEAVY || next_mode == MODE_FUSED;
+    nd.spush = heavy ? s.scur ^ 1u : s.scur;
+    nd.sstamp = heavy ? s.sround + 1u : s.sround;
     nd.qstamp = s.qstamp;
     nd.T = s.T;
     nd.T_lo = nd.slot < kNoSlot ? s.T_lo : 0u;
     nd.ov_cur = s.ov_cur;
     nd.wbase32 = (uint32_t)s.wbase;
     // little work: one block runs the phase without a grid-wide barrier
-    const uint32_t work = next_mode == MODE_REBIN ? nd.count : max(nd.arcs, nd.count + nd.count2);
+    const uint32_t work = next_mode == MODE_REBIN ? nd.count
+                                                  : max(nd.arcs + nd.arcs_h, nd.count + nd.count2 + nd.count_h);
     nd.solo = work <= a.solo_work ? 1u : 0u;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&s);
@@ -817,15 +858,17 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
         const uint4 *ds = reinterpret_cast<const uint4 *>(&nd);
         uint4 *dd = reinterpret_cast<uint4 *>(&c->desc);
         #pragma unroll
-        for (int k = 0; k < 4; ++k) dd[k] = ds[k];
+        for (int k = 0; k < kDescVec; ++k) dd[k] = ds[k];
     }
 }
 
 // Every thread of the block calls it; fills the block's view of the phase.
 __device__ __forceinline__ void read_view(const Ctl *c, BlockView &v) {
-    for (uint32_t i = threadIdx.x; i < 4u + kSlots + 1u; i += blockDim.x) {
-        if (i < 4u) reinterpret_cast<uint4 *>(&v.d)[i] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + i);
-        else v.thr[i - 4u] = __ldcg(&c->thr[i - 4u]);
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kDescVec + kSlots + 1u; i += blockDim.x) {
+        if (i < (uint32_t)kDescVec)
+            reinterpret_cast<uint4 *>(&v.d)[i] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + i);
+        else
+            v.thr[i - kDescVec] = __ldcg(&c->thr[i - kDescVec]);
     }
 }
 
@@ -901,8 +944,13 @@ template <int DT>
 __device__ __forceinline__ void run_phase(const SolveArgs &a, const BlockView &v, BlockAcc &acc, int *slot,
                                           WarpStage *stage, uint32_t gw, uint32_t nw) {
     switch (v.d.mode) {
-    case MODE_LIGHT: phase_arcs<DT, true>(a, v, acc, slot, stage, gw, nw); break;
-    case MODE_HEAVY: phase_arcs<DT, false>(a, v, acc, slot, stage, gw, nw); break;
+    case MODE_LIGHT: phase_arcs<DT, true>(a, v, acc, slot, stage, gw, nw, v.d.count, v.d.arcs, v.d.slot); break;
+    case MODE_HEAVY: phase_arcs<DT, false>(a, v, acc, slot, stage, gw, nw, v.d.count, v.d.arcs, kNoSlot); break;
+    case MODE_FUSED:
+        // heavy arcs of bucket i's S, then the first light round of bucket i+1 (its slot)
+        phase_arcs<DT, false>(a, v, acc, slot, stage, gw, nw, v.d.count_h, v.d.arcs_h, kNoSlot);
+        phase_arcs<DT, true>(a, v, acc, slot, stage, gw, nw, v.d.count, v.d.arcs, v.d.slot);
+        break;
     case MODE_REBIN: phase_rebin<DT>(a, v, acc, stage, gw, nw); break;
     default: break;
     }
@@ -1088,7 +1136,8 @@ cudaError_t allow_stage_smem() {
         (const void *)k_solve_persistent<DSSSP_F32>, (const void *)k_solve_persistent<DSSSP_I32>,
         (const void *)k_phase<DSSSP_F32, MODE_LIGHT>, (const void *)k_phase<DSSSP_I32, MODE_LIGHT>,
         (const void *)k_phase<DSSSP_F32, MODE_HEAVY>, (const void *)k_phase<DSSSP_I32, MODE_HEAVY>,
-        (const void *)k_phase<DSSSP_F32, MODE_REBIN>, (const void *)k_phase<DSSSP_I32, MODE_REBIN>};
+        (const void *)k_phase<DSSSP_F32, MODE_REBIN>, (const void *)k_phase<DSSSP_I32, MODE_REBIN>,
+        (const void *)k_phase<DSSSP_F32, MODE_FUSED>, (const void *)k_phase<DSSSP_I32, MODE_FUSED>};
     for (const void *f : fns)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done[dev] = true;
@@ -1123,6 +1172,7 @@ cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, in
     switch (mode) {
         DSSSP_PHASE_CASE(MODE_LIGHT)
         DSSSP_PHASE_CASE(MODE_HEAVY)
+        DSSSP_PHASE_CASE(MODE_FUSED)
         DSSSP_PHASE_CASE(MODE_REBIN)
     default: break;
     }

@@ -50,7 +50,8 @@ def assert_same(g, src, d, p, d_ref=None, p_ref=None, what=""):
     assert badp.size == 0, f"{what}: {badp.size} predecessors differ, first {badp[:5]} gpu {p[badp[:5]]} ref {p_ref[badp[:5]]}"
 
 
-MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64)]
+# persistent, stepped, a small grid, and heavy passes kept apart from the next bucket (DSSSP_FLAG_NO_FUSE)
+MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64), dict(flags=2)]
 
 
 # ------------------------------------------------------------------ hand-built cases
