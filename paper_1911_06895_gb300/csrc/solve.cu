@@ -32,12 +32,25 @@
 #include <mutex>
 
 #include "dsssp_internal.cuh"
+#include "warp_util.cuh"
 
 namespace dsssp {
 
 namespace {
 
-constexpr uint32_t FULL = 0xffffffffu;
+using wu::flush_arc_entries;
+using wu::flush_ids;
+using wu::FULL;
+using wu::globaltimer;
+using wu::inf_key;
+using wu::kFlush;
+using wu::key_add;
+using wu::kStage;
+using wu::lane_id;
+using wu::lanemask_lt;
+using wu::stage_arc_entry;
+using wu::stage_id;
+
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 #ifndef DSSSP_ILP
 #define DSSSP_ILP 2
@@ -53,39 +66,8 @@ constexpr uint32_t kMinSlice = 32u * kIlp;
 constexpr uint32_t kEntryCost = DSSSP_ENTRY_COST;   // arcs' worth of work per list entry (merge-path weight)
 constexpr uint32_t kNoSlot = kSlots;
 
-__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
-
-__device__ __forceinline__ uint32_t lanemask_lt() {
-    uint32_t m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-__device__ __forceinline__ uint64_t globaltimer() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
 template <typename T>
 __device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; }
-
-// d (+) w on keys: float32 add rounded to nearest (+inf on overflow), or int32
-// add saturated at INT32_MAX. Both operands are below 2^31 for int32.
-template <int DT>
-__device__ __forceinline__ uint32_t key_add(uint32_t dkey, uint32_t wbits) {
-    if (DT == DSSSP_F32) {
-        return __float_as_uint(__fadd_rn(__uint_as_float(dkey), __uint_as_float(wbits)));
-    } else {
-        uint32_t s = dkey + wbits;
-        return s >= KEY_INF_I32 ? KEY_INF_I32 : s;
-    }
-}
-
-template <int DT>
-__device__ __forceinline__ constexpr uint32_t inf_key() {
-    return DT == DSSSP_F32 ? KEY_INF_F32 : KEY_INF_I32;
-}
 
 // Per-block copy of what a phase needs: the descriptor and the window's key
 // thresholds (bucket wbase + t starts at key thr[t]).
@@ -95,11 +77,8 @@ struct BlockView {
 };
 
 // ---------------------------------------------------------------------------
-// Per-warp staging of pushes in shared memory: a list counter (shared by the
-// whole grid) is touched once per kFlush staged entries, not once per 32-arc
-// step. A staging call adds at most 32 entries, so kFlush + 32 slots suffice.
-constexpr uint32_t kFlush = 64;
-constexpr uint32_t kStage = kFlush + 32;
+// Per-warp staging of pushes in shared memory (wu::stage_*): a list counter,
+// shared by the whole grid, is touched once per kFlush staged entries.
 // Improved vertices wait in a per-warp record buffer and are classified 32 at a
 // time, so the stamp exchanges of a whole batch are in flight together instead
 // of one dependent round trip per 32-arc step.
@@ -112,39 +91,6 @@ struct WarpStage {
     uint32_t ov[kStage];                         // overflow
     uint32_t iv[kRec], ik[kRec];                 // improvement records (vertex, new key)
 };
-
-// Append n <= 64 staged (vertex, degree) entries to an arc list; lane l holds
-// entries 2l and 2l+1.
-__device__ __forceinline__ void flush_arc_entries(const uint32_t *bv, const uint32_t *bd, uint32_t n, uint2 *list,
-                                                  unsigned long long *ctr) {
-    const uint32_t lane = lane_id();
-    const uint32_t j = 2u * lane;
-    const bool h0 = j < n, h1 = j + 1u < n;
-    const uint32_t v0 = h0 ? bv[j] : 0u, d0 = h0 ? bd[j] : 0u;
-    const uint32_t v1 = h1 ? bv[j + 1u] : 0u, d1 = h1 ? bd[j + 1u] : 0u;
-    uint32_t incl = d0 + d1;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(FULL, incl, o);
-        if ((int)lane >= o) incl += t;
-    }
-    const uint32_t tot = __shfl_sync(FULL, incl, 31);
-    unsigned long long old = 0;
-    if (lane == 0) old = atomicAdd(ctr, ((unsigned long long)n << 32) | tot);
-    old = __shfl_sync(FULL, old, 0);
-    const uint32_t base = (uint32_t)(old >> 32) + j, off = (uint32_t)old + incl - d0 - d1;
-    if (h0) list[base] = make_uint2(v0, off);
-    if (h1) list[base + 1u] = make_uint2(v1, off + d0);
-}
-
-__device__ __forceinline__ void flush_ids(const uint32_t *bv, uint32_t n, uint32_t *list, uint32_t *counter) {
-    const uint32_t lane = lane_id();
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(counter, n);
-    base = __shfl_sync(FULL, base, 0);
-    if (lane < n) list[base + lane] = bv[lane];
-    if (lane + 32u < n) list[base + lane + 32u] = bv[lane + 32u];
-}
 
 // Append n <= 32 staged slot entries: lanes are grouped by (slot, list); the
 // leader of every group takes its slot counter with one atomic, all groups at
@@ -221,32 +167,6 @@ __device__ __forceinline__ uint32_t ov_index(const PhaseDesc &d) {
     return d.mode == MODE_REBIN ? d.ov_cur ^ 1u : d.ov_cur;
 }
 
-// Stage one entry per pushing lane; flush kFlush entries when the buffer holds
-// that many, keeping the rest (fewer than 32) at its front.
-__device__ __forceinline__ void stage_arc_entry(bool pred, uint32_t v, uint32_t deg, uint32_t *bv, uint32_t *bd,
-                                                uint32_t &cnt, uint2 *list, unsigned long long *ctr) {
-    const uint32_t mask = __ballot_sync(FULL, pred);
-    if (mask == 0u) return;
-    const uint32_t lane = lane_id();
-    if (pred) {
-        const uint32_t k = cnt + __popc(mask & lanemask_lt());
-        bv[k] = v;
-        bd[k] = deg;
-    }
-    cnt += __popc(mask);
-    __syncwarp();
-    if (cnt >= kFlush) {
-        flush_arc_entries(bv, bd, kFlush, list, ctr);
-        const uint32_t rest = cnt - kFlush;
-        uint32_t x = 0, y = 0;
-        if (lane < rest) { x = bv[kFlush + lane]; y = bd[kFlush + lane]; }
-        __syncwarp();
-        if (lane < rest) { bv[lane] = x; bd[lane] = y; }
-        __syncwarp();
-        cnt = rest;
-    }
-}
-
 __device__ __forceinline__ void stage_slot_entry(const SolveArgs &a, bool pred, uint32_t slot, uint32_t v,
                                                  uint32_t deg, WarpStage &ws, uint32_t &cnt) {
     const uint32_t mask = __ballot_sync(FULL, pred);
@@ -265,26 +185,6 @@ __device__ __forceinline__ void stage_slot_entry(const SolveArgs &a, bool pred, 
         if (lane < rest) { x = ws.bt[kFlush + lane]; y = ws.bv[kFlush + lane]; z = ws.bd[kFlush + lane]; }
         __syncwarp();
         if (lane < rest) { ws.bt[lane] = x; ws.bv[lane] = y; ws.bd[lane] = z; }
-        __syncwarp();
-        cnt = rest;
-    }
-}
-
-__device__ __forceinline__ void stage_id(bool pred, uint32_t v, uint32_t *bv, uint32_t &cnt, uint32_t *list,
-                                         uint32_t *counter) {
-    const uint32_t mask = __ballot_sync(FULL, pred);
-    if (mask == 0u) return;
-    const uint32_t lane = lane_id();
-    if (pred) bv[cnt + __popc(mask & lanemask_lt())] = v;
-    cnt += __popc(mask);
-    __syncwarp();
-    if (cnt >= kFlush) {
-        flush_ids(bv, kFlush, list, counter);
-        const uint32_t rest = cnt - kFlush;
-        uint32_t x = 0;
-        if (lane < rest) x = bv[kFlush + lane];
-        __syncwarp();
-        if (lane < rest) bv[lane] = x;
         __syncwarp();
         cnt = rest;
     }

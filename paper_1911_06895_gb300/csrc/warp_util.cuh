@@ -1,4 +1,4 @@
-// warp_util.cuh -- warp-level helpers of the batched solver and the adjoint:
+// warp_util.cuh -- warp-level helpers shared by the solvers (single-source and batched):
 // key arithmetic and per-warp staging of list appends. Not part of the ABI.
 #pragma once
 
