@@ -197,12 +197,13 @@ def run_reference(args, rank, world):
         times.append(dt)
     tot = sum(times)
     value = g.m * len(per_step) * args.steps / tot / 1e9
-    line = {"impl": "reference", "metric": "delta-stepping SSSP GTEPS (m * sources / time)", "value": value,
+    line = {"impl": "reference", "metric": "delta-stepping SSSP GTEPS (m * sources / device time)", "value": value,
             "unit": "GTEPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"rmat{args.scale}_unit_fp32_sources{args.sources}", "n": g.n, "m": g.m,
-                       "sources_per_step": len(per_step)},
+            "config": {"workload": f"rmat{args.scale}_unit_fp32_sources{args.sources}_deltas4", "n": g.n, "m": g.m,
+                       "sources_per_step": len(per_step),
+                       "timing": "host wall time of the CPU oracle (its distances do not depend on Delta)"},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": used, "kind": "oracle",
                              "sample": f"{len(per_step)} sources per step, binary-heap Dijkstra, one source per thread"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -269,13 +270,17 @@ def main():
             split_ms[str(d)] = e0.elapsed_time(e1)
         dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
         pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
-        opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=args.mode)
+        # schedule: the solo threshold per Delta from the tuner (two sample sources, untimed)
+        solo = {}
+        for d in deltas:
+            solo[d] = ds.tune_solo_work(h, srcs[:2], d, stream=stream)[0] if args.mode == 0 else 2048
+        opts = {d: ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=args.mode, solo_work=solo[d]) for d in deltas}
 
         # per-solve statistics (one untimed pass) -> algorithmic bytes
         stats = {}
         for d in deltas:
             stats[d] = [h.solve(s, d, dist=dist, pred=pred, stream=stream, stats=True,
-                                options=ds.make_options(mode=args.mode)).stats for s in srcs]
+                                options=ds.make_options(mode=args.mode, solo_work=solo[d])).stats for s in srcs]
 
         def one_step(record):
             for d in deltas:
@@ -283,7 +288,7 @@ def main():
                     if record is not None:
                         ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                         ev[0].record(stream)
-                    h.solve(s, d, dist=dist, pred=pred, options=opt, stream=stream)
+                    h.solve(s, d, dist=dist, pred=pred, options=opts[d], stream=stream)
                     if record is not None:
                         ev[1].record(stream)
                         record.append((d, ev))
@@ -355,7 +360,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args)
+        e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, solo)
 
     extras = {}
     if world == 1 and not args.no_extras:
@@ -379,7 +384,8 @@ def main():
                        "n": g.n, "m": g.m, "sources": len(srcs), "deltas": deltas, "solves_per_step": solves,
                        "mode": "persistent" if args.mode == 0 else "stepped",
                        "l2": "inputs larger than L2 (arcs %.0f MB per Delta)" % (g.m * 8 / 1e6),
-                       "split_ms": split_ms, "per_delta": per_delta, "parallelism": f"replicas{world}"},
+                       "split_ms": split_ms, "solo_work": {str(d): solo[d] for d in deltas}, "per_delta": per_delta,
+                       "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": measured_traffic(args.scale),
                          "algorithmic_bytes_per_launch": tot_bytes / max(1, solves), "peak_kind": peak_kind,
@@ -597,7 +603,7 @@ def profile_driver(args):
     torch.cuda.synchronize()
 
 
-def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args):
+def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, solo):
     """Public-API end to end: host CSR -> graph -> 256 solves -> results in pinned host memory."""
     rp = torch.from_numpy(g.row_ptr).pin_memory()
     cl = torch.from_numpy(g.col).pin_memory()
@@ -613,9 +619,9 @@ def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args):
             h = ds.Graph(rp.numpy(), cl.numpy(), ww.numpy(), stream=stream)
             dist = torch.empty((2, g.n), dtype=torch.float32, device="cuda")
             pred = torch.empty((2, g.n), dtype=torch.int32, device="cuda")
-            opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
             k = 0
             for d in deltas:
+                opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, solo_work=solo[d])
                 for s in srcs:
                     h.solve(s, d, dist=dist[k & 1], pred=pred[k & 1], options=opt, stream=stream)
                     hd[k & 1].copy_(dist[k & 1], non_blocking=True)

@@ -341,6 +341,13 @@ typedef struct {
 dsssp_status dsssp_autotune(dsssp_graph *const *graphs, int32_t n_graphs, const int32_t *sample_src, int32_t k,
                             const dsssp_tune_options *opt, double *delta_out, double *ms_out, void *stream);
 
+/* Choose dsssp_options.solo_work for single solves of one graph at one Delta: times k sample
+ * solves with the solo threshold at -1 (off), 512, 2048, 8192 and 32768 arcs and returns the
+ * fastest in solo_work_out (ms_out, may be NULL: their device time). Waits for its work.
+ * Errors: INVALID_ARG and those of dsssp_solve. */
+dsssp_status dsssp_tune_solo_work(dsssp_graph *g, const int32_t *sample_src, int32_t k, double delta,
+                                  int32_t *solo_work_out, double *ms_out, void *stream);
+
 /* Choose the team size of a batch (dsssp_options.team_blocks: blocks per instance, 1, 2, 4 or
  * 8) by timing the whole batch at each size: builds the plan the arguments describe (as
  * dsssp_batch_create, outputs written) once per size, runs it twice and keeps the fastest

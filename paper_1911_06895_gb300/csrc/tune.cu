@@ -58,8 +58,10 @@ struct Tried {
     double ms;
 };
 
-// Device time of k dsssp_solve calls at one Delta (split built before timing).
-dsssp_status time_solves(dsssp_graph *g, const int32_t *src, int32_t k, double delta, cudaStream_t st, double *ms) {
+// Device time of k dsssp_solve calls at one Delta (split built before timing);
+// solo_work as in dsssp_options (0: default).
+dsssp_status time_solves(dsssp_graph *g, const int32_t *src, int32_t k, double delta, cudaStream_t st, double *ms,
+                         int32_t solo_work = 0) {
     dsssp_status rc = dsssp_prepare(g, delta, st);
     if (rc != DSSSP_OK) return rc;
     const size_t n = (size_t)g->n;
@@ -73,6 +75,7 @@ dsssp_status time_solves(dsssp_graph *g, const int32_t *src, int32_t k, double d
     dsssp_options o;
     dsssp_options_default(&o);
     o.flags = DSSSP_FLAG_ASYNC;
+    if (solo_work) o.solo_work = solo_work;
     rc = dsssp_solve(g, src[0], delta, dist, pred, &o, nullptr, st);      // warm-up
     if (rc == DSSSP_OK) rc = dsssp_graph_sync(g, st);
     if (rc == DSSSP_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = DSSSP_ERR_CUDA;
@@ -272,6 +275,28 @@ extern "C" dsssp_status dsssp_tune_team_blocks(dsssp_graph *const *graphs, int32
     if (rc != DSSSP_OK) return rc;
     if (best == 0) return DSSSP_ERR_UNSUPPORTED;
     *team_blocks_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return DSSSP_OK;
+}
+
+extern "C" dsssp_status dsssp_tune_solo_work(dsssp_graph *g, const int32_t *sample_src, int32_t k, double delta,
+                                             int32_t *solo_work_out, double *ms_out, void *stream) {
+    if (!g || !sample_src || k < 1 || !solo_work_out || !(delta > 0.0)) return DSSSP_ERR_INVALID_ARG;
+    for (int32_t j = 0; j < k; ++j)
+        if (sample_src[j] < 0 || (int64_t)sample_src[j] >= g->n) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    double best_ms = std::numeric_limits<double>::infinity();
+    int32_t best = 0;
+    for (int32_t sw : {-1, 512, 2048, 8192, 32768}) {
+        double ms = 0.0;
+        dsssp_status rc = time_solves(g, sample_src, k, delta, (cudaStream_t)stream, &ms, sw);
+        if (rc != DSSSP_OK) return rc;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sw;
+        }
+    }
+    *solo_work_out = best;
     if (ms_out) *ms_out = best_ms;
     return DSSSP_OK;
 }

@@ -123,6 +123,8 @@ dsssp_solve_batched = _fn("dsssp_solve_batched", ctypes.c_int,
 dsssp_backward = _fn("dsssp_backward", ctypes.c_int, [_vp, _vp, _vp, _u32, _vp])
 dsssp_autotune = _fn("dsssp_autotune", ctypes.c_int,
                      [_vp, _i32, _vp, _i32, ctypes.POINTER(dsssp_tune_options), _vp, _vp, _vp])
+dsssp_tune_solo_work = _fn("dsssp_tune_solo_work", ctypes.c_int,
+                           [_vp, _vp, _i32, ctypes.c_double, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double), _vp])
 dsssp_tune_team_blocks = _fn("dsssp_tune_team_blocks", ctypes.c_int,
                              [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_i32),
                               ctypes.POINTER(ctypes.c_double), _vp])
@@ -130,7 +132,8 @@ dsssp_tune_team_blocks = _fn("dsssp_tune_team_blocks", ctypes.c_int,
 EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create", "dsssp_graph_destroy",
             "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc",
             "dsssp_batch_create", "dsssp_batch_run", "dsssp_batch_sync", "dsssp_batch_destroy",
-            "dsssp_solve_batched", "dsssp_backward", "dsssp_autotune", "dsssp_tune_team_blocks"]
+            "dsssp_solve_batched", "dsssp_backward", "dsssp_autotune", "dsssp_tune_team_blocks",
+            "dsssp_tune_solo_work"]
 
 NOALLOC_MAX_VERTICES = 1 << 17
 
@@ -411,3 +414,14 @@ def tune_team_blocks(graphs, deltas, sources, src_graph=None, stream=None):
                                  _ptr_array([d.data_ptr() for d in dist]), None, ctypes.byref(tb), ctypes.byref(ms),
                                  _stream_ptr(stream)), "dsssp_tune_team_blocks")
     return int(tb.value), float(ms.value)
+
+
+def tune_solo_work(graph, sample_sources, delta, stream=None):
+    """Solo threshold (dsssp_options.solo_work) at which single solves run fastest; returns (solo_work, ms)."""
+    k = len(sample_sources)
+    sw = _i32(0)
+    ms = ctypes.c_double(0.0)
+    check(dsssp_tune_solo_work(graph.handle, (ctypes.c_int32 * k)(*[int(s) for s in sample_sources]), k,
+                               float(delta), ctypes.byref(sw), ctypes.byref(ms), _stream_ptr(stream)),
+          "dsssp_tune_solo_work")
+    return int(sw.value), float(ms.value)

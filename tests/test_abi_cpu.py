@@ -65,6 +65,7 @@ def test_null_arguments_rejected_without_gpu():
     assert ds.dsssp_autotune(None, 1, None, 1, None, None, None, None) == ds.DSSSP_ERR_INVALID_ARG
     assert ds.dsssp_tune_team_blocks(None, 1, None, 1, None, None, None, None, None, None,
                                      None) == ds.DSSSP_ERR_INVALID_ARG
+    assert ds.dsssp_tune_solo_work(None, None, 1, 1.0, None, None, None) == ds.DSSSP_ERR_INVALID_ARG
 
 
 def test_struct_layout_matches_header():

@@ -81,3 +81,13 @@ def test_tune_team_blocks(ds):
     d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, sources[0])
     assert np.array_equal(b.dist[0].cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
     b.close()
+
+
+def test_tune_solo_work(ds):
+    g, sources, _ = W.rmat22_unit(scale=14, n_sources=3)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    sw, ms = ds.tune_solo_work(h, sources[:2], 0.05)
+    assert sw in (-1, 512, 2048, 8192, 32768) and ms > 0
+    r = h.solve(sources[2], 0.05, options=ds.make_options(solo_work=sw))
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, sources[2])
+    assert np.array_equal(r.dist.cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
