@@ -276,6 +276,14 @@ def main():
             solo[d] = ds.tune_solo_work(h, srcs[:2], d, stream=stream)[0] if args.mode == 0 else 2048
         opts = {d: ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=args.mode, solo_work=solo[d]) for d in deltas}
 
+        # arcs out of reached vertices per source (Delta does not change which vertices are reached)
+        deg = torch.from_numpy(np.diff(g.row_ptr)).to("cuda")
+        m_reached = {}
+        for s in srcs:
+            h.solve(s, deltas[0], dist=dist, pred=pred, stream=stream,
+                    options=ds.make_options(mode=args.mode, solo_work=solo[deltas[0]]))
+            m_reached[s] = int(deg[torch.isfinite(dist)].sum().item())
+
         # per-solve statistics (one untimed pass) -> algorithmic bytes
         stats = {}
         for d in deltas:
@@ -321,7 +329,8 @@ def main():
         tot_bytes, tot_ms, tot_light_b, tot_light_ns = 0, 0.0, 0, 0
         for d in deltas:
             ms_d = sum(ev[0].elapsed_time(ev[1]) for dd, ev in recs if dd == d)
-            per_delta[str(d)] = {"gteps": g.m * len(srcs) / (ms_d * 1e-3) / 1e9, "ms_per_solve": ms_d / len(srcs)}
+            per_delta[str(d)] = {"gteps": g.m * len(srcs) / (ms_d * 1e-3) / 1e9, "ms_per_solve": ms_d / len(srcs),
+                                 "gteps_reached": sum(m_reached.values()) / (ms_d * 1e-3) / 1e9}
             b = sum(algorithmic_bytes(st, g.n) for st in stats[d])
             tot_bytes += b
             tot_ms += ms_d
@@ -384,7 +393,8 @@ def main():
                        "n": g.n, "m": g.m, "sources": len(srcs), "deltas": deltas, "solves_per_step": solves,
                        "mode": "persistent" if args.mode == 0 else "stepped",
                        "l2": "inputs larger than L2 (arcs %.0f MB per Delta)" % (g.m * 8 / 1e6),
-                       "split_ms": split_ms, "solo_work": {str(d): solo[d] for d in deltas}, "per_delta": per_delta,
+                       "split_ms": split_ms, "solo_work": {str(d): solo[d] for d in deltas},
+                       "mean_reached_arcs": sum(m_reached.values()) / len(srcs), "per_delta": per_delta,
                        "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": measured_traffic(args.scale),

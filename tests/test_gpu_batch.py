@@ -141,6 +141,33 @@ def test_cluster_teams_tape_and_graphs(ds):
     b.close()
 
 
+def test_batch_run_inside_a_torch_cuda_graph(ds):
+    """A batch run is one CUDA-graph launch with no allocation or host wait, so a caller can
+    capture it in a graph of its own and replay it."""
+    g, sources, _ = W.rmat22_unit(scale=13, n_sources=6)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = batch(ds, h, [0.1], sources)
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        b.run(side)                                      # warm-up outside the capture
+    b.sync(stream=side)
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg, stream=side):
+        b.run(side)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for rep in range(2):
+        for d in b.dist:
+            d.fill_(-1.0)
+        torch.cuda.synchronize()
+        cg.replay()
+        torch.cuda.synchronize()
+        ds_, ps_ = fetch(b)
+        for k, s in enumerate(sources):
+            same(ds_[k], ps_[k], refd[k], refp[k], f"replay {rep} src {s}")
+    b.sync()
+    b.close()
+
+
 def edge_graphs():
     out = []
     out.append((graphgen.from_arcs(1, [], np.zeros(0, np.float32), dtype=np.float32), 0, 1.0))
