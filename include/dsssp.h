@@ -270,7 +270,9 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
                                 const dsssp_options *opt, void *stream, dsssp_batch **out);
 
 /* Enqueue one run of every instance on `stream`: a single launch of the plan's CUDA graph
- * (queue reset + the persistent kernel). Does not wait. Errors: INVALID_ARG, CUDA. */
+ * (queue reset + the persistent kernel). While `stream` is being captured into a caller's CUDA
+ * graph, the two operations are enqueued directly and become nodes of that graph. Allocates
+ * nothing and does not wait. Errors: INVALID_ARG, CUDA. */
 dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream);
 
 /* Wait for `stream`, then return (and clear) the first device-side status of the runs and

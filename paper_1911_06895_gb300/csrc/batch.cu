@@ -848,6 +848,7 @@ struct dsssp_batch {
     BatchArgs args{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    const void *kfn = nullptr;              // the forward kernel of this plan
     void *h_ptrs = nullptr;                 // pinned staging for backward pointer tables
     long long max_phases = 0;
 };
@@ -1122,6 +1123,7 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
         mp.pitch = 4;
         e = cudaGraphAddMemsetNode(&n_memset, b->graph, nullptr, 0, &mp);
     }
+    b->kfn = kfn;
     if (e == cudaSuccess) {
         void *kargs[] = {&b->args};
         cudaKernelNodeParams kp{};
@@ -1151,7 +1153,28 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
 dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream) {
     if (!b) return DSSSP_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
-    DSSSP_TRY(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DSSSP_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusActive) {
+        // the caller is recording a graph of its own: the same two operations go in as its nodes
+        DSSSP_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), st));
+        cudaLaunchConfig_t cfg{};
+        cudaLaunchAttribute attr{};
+        attr.id = cudaLaunchAttributeClusterDimension;
+        attr.val.clusterDim.x = b->csize;
+        attr.val.clusterDim.y = 1;
+        attr.val.clusterDim.z = 1;
+        cfg.gridDim = dim3(b->teams * b->csize);
+        cfg.blockDim = dim3(kTeamThreads);
+        cfg.stream = st;
+        cfg.attrs = &attr;
+        cfg.numAttrs = 1;
+        void *kargs[] = {&b->args};
+        DSSSP_TRY(cudaLaunchKernelExC(&cfg, b->kfn, kargs));
+    } else {
+        DSSSP_TRY(cudaGraphLaunch(b->exec, st));
+    }
     b->ran = true;
     return DSSSP_OK;
 }
