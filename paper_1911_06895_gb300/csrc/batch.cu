@@ -942,22 +942,33 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
         csize = 1;
         while (csize < 8 && (long long)n_inst * csize <= blocks_max) csize *= 2;
     }
+    // co-resident teams of that size (an automatic size halves until clusters of it fit)
+    const bool auto_size = o.team_blocks == 0;
     long long max_teams = blocks_max / csize;
-    if (csize > 1) {
+    while (csize > 1) {
         cudaLaunchConfig_t cfg{};
         cudaLaunchAttribute attr{};
         attr.id = cudaLaunchAttributeClusterDimension;
         attr.val.clusterDim.x = (unsigned)csize;
         attr.val.clusterDim.y = 1;
         attr.val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)(csize * max_teams));
+        cfg.gridDim = dim3((unsigned)(csize * (blocks_max / csize)));
         cfg.blockDim = dim3(kTeamThreads);
         cfg.attrs = &attr;
         cfg.numAttrs = 1;
         int clusters = 0;
-        if ((e = cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg)) != cudaSuccess) return fail(cuda_status(e));
-        if (clusters < 1) return fail(DSSSP_ERR_UNSUPPORTED);
-        max_teams = clusters;
+        e = cudaOccupancyMaxActiveClusters(&clusters, kfn, &cfg);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            clusters = 0;
+        }
+        if (clusters >= 1) {
+            max_teams = clusters;
+            break;
+        }
+        if (!auto_size) return fail(e != cudaSuccess ? cuda_status(e) : DSSSP_ERR_UNSUPPORTED);
+        csize /= 2;
+        max_teams = blocks_max / csize;
     }
     unsigned long long cap = 1;
     size_t sum_m = 0, sum_n_inst = 0;

@@ -119,6 +119,21 @@ def test_cluster_teams(ds, team_blocks):
             b.close()
 
 
+def test_cluster_teams_int32(ds):
+    g, srcs, _ = W.rmat14_int()
+    sources = srcs + [int(s) for s in graphgen.random_sources(g, 7, 21)]
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    for tb in (2, 8):
+        b = batch(ds, h, [32.0], sources, team_blocks=tb)
+        b.run()
+        b.sync()
+        ds_, ps_ = fetch(b)
+        for k, s in enumerate(sources):
+            same(ds_[k], ps_[k], refd[k], refp[k], f"int32 team_blocks {tb} src {s}")
+        b.close()
+
+
 def test_cluster_teams_tape_and_graphs(ds):
     g, sources, _ = W.rmat20_lognormal(scale=13, n_sources=6)
     cs = [graphgen.random_costs(g.n, 70 + k) for k in range(len(sources))]
