@@ -64,7 +64,7 @@ def measured_traffic(scale: int):
     import hashlib
     csrc = os.path.join(ROOT, "paper_1911_06895_gb300", "csrc")
     h = hashlib.sha256()
-    for f in ("solve.cu", "dsssp_internal.cuh"):
+    for f in ("solve.cu", "dsssp_internal.cuh", "warp_util.cuh"):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return TRAFFIC_BYTES_PER_LAUNCH if (scale == 22 and h.hexdigest() == TRAFFIC_SOURCE_SHA256) else None
@@ -230,6 +230,9 @@ def main():
                     help="profiling driver: one batch of this many scale-20 R-MAT sources at --profile-delta")
     ap.add_argument("--profile-delta", default="0.1",
                     help="comma-separated Deltas, or 'all' for every Delta of the sweep")
+    ap.add_argument("--no-fuse", action="store_true",
+                    help="profiling driver: keep heavy passes and light rounds in separate phases "
+                         "(with --mode 1 every phase type is then its own kernel)")
     args = ap.parse_args()
     if args.profile_solves:
         profile_driver(args)
@@ -604,7 +607,7 @@ def profile_driver(args):
     h = ds.Graph(g.row_ptr, g.col, g.w)
     for d in deltas:
         h.prepare(d)
-    opt = ds.make_options(mode=args.mode)
+    opt = ds.make_options(mode=args.mode, flags=ds.DSSSP_FLAG_NO_FUSE if args.no_fuse else 0)
     for d in deltas:
         for s in srcs[:args.profile_solves]:
             r = h.solve(s, d, options=opt, stats=True)

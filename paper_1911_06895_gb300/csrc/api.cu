@@ -327,7 +327,7 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     if (opt.mode == DSSSP_MODE_PERSISTENT) {
         DSSSP_TRY(launch_solve_persistent(a, grid, opt.block_size, st));
     } else {
-        // host-driven loop: one kernel per phase, the serial step as a 1-thread kernel
+        // host-driven loop: one kernel per phase, the serial step as a 1-warp kernel
         for (int64_t ph = 0;; ++ph) {
             DSSSP_TRY(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
             DSSSP_TRY(cudaStreamSynchronize(st));

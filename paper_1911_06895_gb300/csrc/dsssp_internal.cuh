@@ -120,9 +120,10 @@ constexpr uint32_t kSlots = 32;
 // positions and arc offsets agree and a phase splits the list's flattened arcs
 // evenly over all warps. A vertex's arc segment comes from vinfo.
 //
-// Control block. The serial step of a barrier (one thread) loads SerialState
-// and the list counters in one batch, decides the next phase in registers and
-// publishes a PhaseDesc that every block reads with four 16-byte loads.
+// Control block. The serial step of a barrier (one warp) loads SerialState, the
+// list counters and the window's slot counters in one batch, decides the next
+// phase in registers and publishes a PhaseDesc that every block reads with
+// 16-byte loads, together with the window's thresholds and the error word.
 
 // Everything a block needs to run a phase (64 bytes).
 struct alignas(64) PhaseDesc {

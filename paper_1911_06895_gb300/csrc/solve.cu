@@ -28,7 +28,7 @@
 // barrier wait is bounded by timeout_ns and ends the kernel with
 // DSSSP_ERR_TIMEOUT instead of hanging. Phases with little work run on block 0
 // alone (solo). DSSSP_MODE_STEPPED launches one kernel per phase and runs the
-// serial step as a 1-thread kernel.
+// serial step as a 1-warp kernel.
 #include <mutex>
 
 #include "dsssp_internal.cuh"
@@ -74,6 +74,7 @@ __device__ __forceinline__ T vload(const T *p) { return *(const volatile T *)p; 
 struct BlockView {
     PhaseDesc d;
     uint32_t thr[kSlots + 1];
+    int32_t err;            // the control block's error word when the view was taken
 };
 
 // ---------------------------------------------------------------------------
@@ -216,10 +217,12 @@ __device__ __forceinline__ void drain_pushes(const SolveArgs &a, const PhaseDesc
 // ---------------------------------------------------------------------------
 // Queue v for bucket i (its key is now below T): once per phase into the next
 // frontier (its light segment), once per bucket into S (its heavy segment).
-// The loads are issued together with the stamp exchange.
+// The loads are issued together with the stamp exchange. Arc segments (vinfo)
+// are read once per list entry or improvement, packed[] once per relaxed arc:
+// segment reads are evict-first so that packed[] keeps its place in L2.
 __device__ __forceinline__ void queue_near(const SolveArgs &a, const PhaseDesc &d, uint32_t v, Push &p) {
     const uint32_t prev = atomicExch(a.near_stamp + v, d.qstamp);
-    const uint4 vi = a.vinfo[v];
+    const uint4 vi = __ldcs(a.vinfo + v);
     const uint32_t ss = __ldcg(a.s_stamp + v);
     if (prev == d.qstamp) return;
     p.fdeg = vi.y - vi.x;
@@ -251,7 +254,7 @@ __device__ __forceinline__ void queue_later(const SolveArgs &a, const BlockView 
         const uint32_t t = slot_of(bvw.thr, ckey);
         const uint32_t stamp = bvw.d.wbase32 + t + 1u;    // bucket + 1: one entry per (vertex, bucket)
         const uint32_t prev = atomicExch(a.b_stamp + v, stamp);
-        const uint4 vi = a.vinfo[v];
+        const uint4 vi = __ldcs(a.vinfo + v);
         if (prev != stamp) {
             p.b = true;
             p.slot = t;
@@ -407,7 +410,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
                 wv = en.x < a.n ? en.x : 0u;          // defensive: ids come from device lists
                 woff = en.y;
                 const uint32_t k = (uint32_t)(__ldcg(a.packed + wv) >> 32);
-                const uint4 vi = a.vinfo[wv];
+                const uint4 vi = __ldcs(a.vinfo + wv);
                 wbeg = LIGHT ? vi.x : vi.y;
                 wkey = (T_lo == 0u || k >= T_lo) ? k : inf_key<DT>();
             } else {
@@ -552,13 +555,17 @@ __device__ void phase_rebin(const SolveArgs &a, const BlockView &bvw, BlockAcc &
 }
 
 // ---------------------------------------------------------------------------
-// Serial step: runs on one thread after every block has finished a phase.
-// Loads the serial state and the list counters in one batch, decides the next
-// phase (the control flow of Fig. 1) in registers, resets consumed counters
-// and publishes the next PhaseDesc.
+// Serial step: one warp, after every block has finished a phase. Every load is
+// in one batch: the serial state, the phase that ended and the list counters
+// (the same words on all lanes), and lane t's bucket slot t (its counters and
+// key threshold). Every lane then takes the same decision (the control flow of
+// Fig. 1) in registers; lane 0 resets consumed counters and publishes the next
+// PhaseDesc. With `out`, the warp also writes the next phase's view there.
 template <int DT>
-__device__ __noinline__ void serial_step(const SolveArgs &a) {
+__device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
     Ctl *c = a.ctl;
+    const uint32_t lane = lane_id();
+    const bool l0 = lane == 0u;
     SerialState s;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&c->ss);
@@ -573,9 +580,28 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
     unsigned long long ctrF[2] = {__ldcg(&c->ctrF[0]), __ldcg(&c->ctrF[1])};
     unsigned long long ctrS[2] = {__ldcg(&c->ctrS[0]), __ldcg(&c->ctrS[1])};
     const uint32_t nov[2] = {__ldcg(&c->nOV[0]), __ldcg(&c->nOV[1])};
-    const uint32_t ov_min = __ldcg(&c->ov_min);
+    uint32_t ov_min = __ldcg(&c->ov_min);
     const uint64_t t_first = __ldcg(&c->t_first);
+    int32_t err = __ldcg(&c->err);
+    // bucket slot `lane` of the window (kSlots == 32 lanes) and the window's end
+    const unsigned long long my_sl = __ldcg(&c->ctrSL[lane]);
+    const uint32_t my_sh = __ldcg(&c->nSH[lane]);
+    uint32_t my_th = __ldcg(&c->thr[lane]);
+    uint32_t th_end = __ldcg(&c->thr[kSlots]);
     const uint64_t now = globaltimer();
+    // the first slot past the current bucket: its own state for the fusion
+    // check, the first non-empty one for the search of the next bucket (the
+    // consumed slot of the current bucket lies below it)
+    const int first = (int)(s.bucket - s.wbase + 1);
+    const uint32_t ne = __ballot_sync(FULL, (int)lane >= first && ((my_sl >> 32) != 0ull || my_sh != 0u));
+    const int found = ne ? __ffs(ne) - 1 : -1;
+    const int fl = found < 0 ? 0 : found;
+    const unsigned long long fsl = __shfl_sync(FULL, my_sl, fl);
+    const uint32_t fsh = __shfl_sync(FULL, my_sh, fl);
+    const uint32_t flo = __shfl_sync(FULL, my_th, fl);
+    const uint32_t fhi_n = __shfl_sync(FULL, my_th, (fl + 1) & 31);
+    const uint32_t fhi = fl + 1 < (int)kSlots ? fhi_n : th_end;
+
     const uint64_t dt = now - s.t_last;
     if (t_first > s.t_last && t_first <= now) {      // persistent mode only
         s.st[ST_NSFIRST] += (long long)(t_first - s.t_last);
@@ -591,7 +617,11 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
     nd.slot = kNoSlot;
     bool done = false;
     if (s.phases >= a.max_phases) {
-        atomicCAS(&c->err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
+        if (l0) {
+            const int prev = atomicCAS(&c->err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
+            err = prev != 0 ? prev : (int)DSSSP_ERR_NOT_CONVERGED;
+        }
+        err = __shfl_sync(FULL, err, 0);
         done = true;
     } else {
         switch (mode) {
@@ -599,18 +629,20 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
             s.st[ST_LIGHT] += 1;
             if (od.slot < kNoSlot) {               // the bucket's slot is consumed
                 s.st[ST_VLIGHT] += (long long)od.count;
-                c->ctrSL[od.slot] = 0ull;
-                c->nSH[od.slot] = 0u;
+                if (l0) {
+                    c->ctrSL[od.slot] = 0ull;
+                    c->nSH[od.slot] = 0u;
+                }
             } else {
                 s.st[ST_VLIGHT] += (long long)(ctrF[s.cur] >> 32);
-                c->ctrF[s.cur] = 0ull;
+                if (l0) c->ctrF[s.cur] = 0ull;
                 ctrF[s.cur] = 0ull;
             }
             break;
         case MODE_HEAVY:
             s.st[ST_HEAVY] += 1;
             s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
-            c->ctrS[s.scur] = 0ull;
+            if (l0) c->ctrS[s.scur] = 0ull;
             ctrS[s.scur] = 0ull;
             s.scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
             s.sround += 1u;
@@ -620,16 +652,18 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
             s.st[ST_HEAVY] += 1;
             s.st[ST_VLIGHT] += (long long)od.count;
             s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
-            c->ctrSL[od.slot] = 0ull;
-            c->nSH[od.slot] = 0u;
-            c->ctrS[s.scur] = 0ull;
+            if (l0) {
+                c->ctrSL[od.slot] = 0ull;
+                c->nSH[od.slot] = 0u;
+                c->ctrS[s.scur] = 0ull;
+            }
             ctrS[s.scur] = 0ull;
             s.scur ^= 1u;
             s.sround += 1u;
             break;
         case MODE_REBIN:
             s.st[ST_REBIN] += 1;
-            c->nOV[s.ov_cur] = 0u;
+            if (l0) c->nOV[s.ov_cur] = 0u;
             s.ov_cur ^= 1u;
             break;
         default:
@@ -651,25 +685,16 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
             // same phase as bucket i's heavy pass: heavy weights exceed Delta, so the
             // heavy pass only adds to buckets >= i+1, and what it adds to i+1 is relaxed
             // in i+1's later rounds (the fixed point does not depend on the order).
-            const int j = (int)(s.bucket - s.wbase + 1);
-            unsigned long long jsl = 0ull;
-            uint32_t jsh = 0u, jlo = 0u, jhi = 0u;
-            if (a.fuse && j >= 0 && j < (int)kSlots) {
-                jsl = __ldcg(&c->ctrSL[j]);
-                jsh = __ldcg(&c->nSH[j]);
-                jlo = __ldcg(&c->thr[j]);
-                jhi = __ldcg(&c->thr[j + 1]);
-            }
-            if ((jsl >> 32) != 0ull || jsh != 0u) {
+            if (a.fuse && first >= 0 && found == first) {
                 next_mode = MODE_FUSED;
                 s.bucket += 1;
                 s.st[ST_BUCKETS] += 1;
-                s.T_lo = jlo;
-                s.T = jhi;
-                nd.slot = (uint32_t)j;
-                nd.count = (uint32_t)(jsl >> 32);
-                nd.arcs = (uint32_t)jsl;
-                nd.count2 = jsh;
+                s.T_lo = flo;
+                s.T = fhi;
+                nd.slot = (uint32_t)found;
+                nd.count = (uint32_t)(fsl >> 32);
+                nd.arcs = (uint32_t)fsl;
+                nd.count2 = fsh;
                 nd.count_h = (uint32_t)(ctrS[s.scur] >> 32);
                 nd.arcs_h = (uint32_t)ctrS[s.scur];
             } else {
@@ -677,59 +702,39 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
                 nd.count = (uint32_t)(ctrS[s.scur] >> 32);
                 nd.arcs = (uint32_t)ctrS[s.scur];
             }
-        } else {
-            // next non-empty bucket of the window: slot counters read 8 at a time
-            const int first = (int)(s.bucket - s.wbase + 1);   // slots before it are consumed
-            int found = -1;
-            unsigned long long fsl = 0ull;
-            uint32_t fsh = 0u;
-            for (int t0 = first < 0 ? 0 : first; t0 < (int)kSlots && found < 0; t0 += 8) {
-                unsigned long long sl[8];
-                uint32_t sh[8];
-                #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int t = t0 + k < (int)kSlots ? t0 + k : (int)kSlots - 1;
-                    sl[k] = __ldcg(&c->ctrSL[t]);
-                    sh[k] = __ldcg(&c->nSH[t]);
-                }
-                #pragma unroll
-                for (int k = 0; k < 8; ++k)
-                    if (found < 0 && t0 + k < (int)kSlots && ((sl[k] >> 32) != 0ull || sh[k] != 0u)) {
-                        found = t0 + k;
-                        fsl = sl[k];
-                        fsh = sh[k];
-                    }
+        } else if (found >= 0) {                   // next non-empty bucket of the window
+            s.bucket = s.wbase + found;
+            s.st[ST_BUCKETS] += 1;
+            s.T_lo = flo;
+            s.T = fhi;
+            next_mode = MODE_LIGHT;
+            nd.slot = (uint32_t)found;
+            nd.count = (uint32_t)(fsl >> 32);
+            nd.arcs = (uint32_t)fsl;
+            nd.count2 = fsh;
+        } else if (nov[s.ov_cur] != 0u) {
+            // window used up: the next one starts at the smallest overflow key;
+            // lane t resets slot t and sets its threshold, lane 0 also the window's end
+            c->ctrSL[lane] = 0ull;
+            c->nSH[lane] = 0u;
+            if (ov_min < inf_key<DT>()) {
+                const int64_t w = bucket_of_key(ov_min, DT, a.delta);
+                s.wbase = w;
+                s.bucket = w - 1;
+                my_th = w + lane < INT64_MAX ? bucket_floor_key(w + lane, DT, a.delta) : inf_key<DT>();
+                if (lane == 1u && my_th <= ov_min) my_th = ov_min + 1u;   // the smallest key lands in slot 0
+                th_end = w + kSlots < INT64_MAX ? bucket_floor_key(w + kSlots, DT, a.delta) : inf_key<DT>();
+            } else {                               // only stale entries remain: drop them all
+                my_th = inf_key<DT>();
+                th_end = inf_key<DT>();
             }
-            if (found >= 0) {
-                s.bucket = s.wbase + found;
-                s.st[ST_BUCKETS] += 1;
-                s.T_lo = __ldcg(&c->thr[found]);
-                s.T = __ldcg(&c->thr[found + 1]);
-                next_mode = MODE_LIGHT;
-                nd.slot = (uint32_t)found;
-                nd.count = (uint32_t)(fsl >> 32);
-                nd.arcs = (uint32_t)fsl;
-                nd.count2 = fsh;
-            } else if (nov[s.ov_cur] != 0u) {
-                // window used up: the next one starts at the smallest overflow key
-                #pragma unroll
-                for (int t = 0; t < (int)kSlots; ++t) { c->ctrSL[t] = 0ull; c->nSH[t] = 0u; }
-                if (ov_min < inf_key<DT>()) {
-                    const int64_t w = bucket_of_key(ov_min, DT, a.delta);
-                    s.wbase = w;
-                    s.bucket = w - 1;
-                    for (int t = 0; t <= (int)kSlots; ++t) {
-                        uint32_t th = w + t < INT64_MAX ? bucket_floor_key(w + t, DT, a.delta) : inf_key<DT>();
-                        if (t == 1 && th <= ov_min) th = ov_min + 1u;   // the smallest key lands in slot 0
-                        c->thr[t] = th;
-                    }
-                } else {                           // only stale entries remain: drop them all
-                    for (int t = 0; t <= (int)kSlots; ++t) c->thr[t] = inf_key<DT>();
-                }
+            c->thr[lane] = my_th;
+            if (l0) {
+                c->thr[kSlots] = th_end;
                 c->ov_min = inf_key<DT>();
-                next_mode = MODE_REBIN;
-                nd.count = nov[s.ov_cur];
             }
+            next_mode = MODE_REBIN;
+            nd.count = nov[s.ov_cur];
         }
     }
     if (next_mode == MODE_DONE) s.st[ST_NSTOTAL] = (long long)(now - s.t_start);
@@ -750,7 +755,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
     const uint32_t work = next_mode == MODE_REBIN ? nd.count
                                                   : max(nd.arcs + nd.arcs_h, nd.count + nd.count2 + nd.count_h);
     nd.solo = work <= a.solo_work ? 1u : 0u;
-    {
+    if (l0) {
         const uint4 *src = reinterpret_cast<const uint4 *>(&s);
         uint4 *dst = reinterpret_cast<uint4 *>(&c->ss);
         #pragma unroll
@@ -760,15 +765,25 @@ __device__ __noinline__ void serial_step(const SolveArgs &a) {
         #pragma unroll
         for (int k = 0; k < kDescVec; ++k) dd[k] = ds[k];
     }
+    if (out != nullptr) {
+        out->thr[lane] = my_th;
+        if (l0) {
+            out->thr[kSlots] = th_end;
+            out->d = nd;
+            out->err = err;
+        }
+    }
 }
 
 // Every thread of the block calls it; fills the block's view of the phase.
 __device__ __forceinline__ void read_view(const Ctl *c, BlockView &v) {
-    for (uint32_t i = threadIdx.x; i < (uint32_t)kDescVec + kSlots + 1u; i += blockDim.x) {
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kDescVec + kSlots + 2u; i += blockDim.x) {
         if (i < (uint32_t)kDescVec)
             reinterpret_cast<uint4 *>(&v.d)[i] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + i);
-        else
+        else if (i < (uint32_t)kDescVec + kSlots + 1u)
             v.thr[i - kDescVec] = __ldcg(&c->thr[i - kDescVec]);
+        else
+            v.err = __ldcg(&c->err);
     }
 }
 
@@ -795,32 +810,47 @@ __device__ __forceinline__ void acc_init(BlockAcc &acc) {
 }
 
 // Grid-wide barrier with a serial step, every wait bounded by timeout_ns.
-// With run_serial false (after a solo stretch, whose serial steps block 0
+// Warp 0 of every block arrives; in the last block to arrive it runs the serial
+// step. With run_serial false (after a solo stretch, whose serial steps block 0
 // already ran) the last arrival only releases; blocks that wait through a solo
 // stretch poll slowly so that they do not load the L2 the solo block uses.
+// Returns false when this block saw the error word set or gave up waiting; the
+// error word is otherwise checked in the next view.
 template <int DT>
 __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool run_serial, bool patient) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32u) {
+        const uint32_t lane = threadIdx.x;
         Ctl *c = a.ctl;
-        flush_ov_min(c, acc, inf_key<DT>());
-        __threadfence();
-        const unsigned gen = vload(&c->bar_gen);
-        const unsigned arrived = atomicAdd(&c->bar_count, 1u);
-        if (run_serial && arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
+        unsigned gen = 0u, arrived = 0u;
+        if (lane == 0u) {
+            flush_ov_min(c, acc, inf_key<DT>());
+            __threadfence();
+            gen = vload(&c->bar_gen);
+            arrived = atomicAdd(&c->bar_count, 1u);
+            if (run_serial && arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
+        }
+        arrived = __shfl_sync(FULL, arrived, 0);
+        int ok = 1;
         if (arrived == a.nblocks - 1u) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            if (run_serial) serial_step<DT>(a);
-            __threadfence();
-            atomicExch(&c->bar_gen, gen + 1u);
-        } else {
+            if (lane == 0u) {
+                atomicExch(&c->bar_count, 0u);
+                __threadfence();
+            }
+            __syncwarp();
+            if (run_serial) serial_step<DT>(a, nullptr);
+            __syncwarp();
+            if (lane == 0u) {
+                __threadfence();
+                atomicExch(&c->bar_gen, gen + 1u);
+            }
+        } else if (lane == 0u) {
             // bounded wait: timeout_ns without progress (a solo block's serial
             // steps advance ss.phases, which restarts the clock)
             uint64_t t0 = globaltimer();
             int64_t seen = patient ? vload(&c->ss.phases) : 0;
             while (vload(&c->bar_gen) == gen) {
-                if (vload(&c->err) != 0) break;
+                if (vload(&c->err) != 0) { ok = 0; break; }
                 const uint64_t now = globaltimer();
                 if (patient) {
                     const int64_t ph = vload(&c->ss.phases);
@@ -828,13 +858,14 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool 
                 }
                 if ((int64_t)(now - t0) > a.timeout_ns) {
                     atomicCAS(&c->err, 0, (int)DSSSP_ERR_TIMEOUT);
+                    ok = 0;
                     break;
                 }
                 if (patient) __nanosleep(500);
             }
             __threadfence();
         }
-        *s_ok = vload(&c->err) == 0;
+        if (lane == 0u) *s_ok = ok;
     }
     __syncthreads();
     return *s_ok != 0;
@@ -878,9 +909,9 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(Solv
             __syncthreads();
         }
         have_view = false;
-        if (view.d.mode == MODE_DONE) break;
+        if (view.err != 0 || view.d.mode == MODE_DONE) break;
         // A solo phase (little work) runs on block 0 only: its phases follow each
-        // other with block-level synchronisation and the serial step in thread 0,
+        // other with block-level synchronisation and the serial step in warp 0,
         // while the other blocks wait in the grid barrier until a phase with work
         // for the whole grid (or the end) comes.
         const bool solo = view.d.solo != 0u;
@@ -888,21 +919,20 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(Solv
         if (solo && blockIdx.x == 0) {
             __threadfence();             // list entries and flags reach L2 before the serial step reads them
             __syncthreads();
-            if (threadIdx.x == 0) {
-                flush_ov_min(a.ctl, acc, inf_key<DT>());
-                __threadfence();
-                serial_step<DT>(a);
-                __threadfence();
-                s_ok = vload(&a.ctl->err) == 0;
+            if (threadIdx.x < 32u) {     // warp 0: the serial step, which also writes the block's next view
+                if (threadIdx.x == 0u) {
+                    flush_ov_min(a.ctl, acc, inf_key<DT>());
+                    __threadfence();
+                }
+                __syncwarp();
+                serial_step<DT>(a, &view);
+                __syncwarp();
+                if (threadIdx.x == 0u) __threadfence();
             }
             __syncthreads();
-            if (!s_ok) break;
-            read_view(a.ctl, view);
-            __syncthreads();
-            if (view.d.solo && view.d.mode != MODE_DONE) {
-                have_view = true;        // next solo phase right away
-                continue;
-            }
+            if (view.err != 0) break;
+            have_view = true;
+            if (view.d.solo && view.d.mode != MODE_DONE) continue;   // next solo phase right away
             if (!grid_barrier<DT>(a, acc, &s_ok, false, false)) break;   // release the waiting blocks
         } else if (solo) {
             if (!grid_barrier<DT>(a, acc, &s_ok, false, true)) break;
@@ -934,9 +964,10 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_phase(SolveArgs a) {
     }
 }
 
+// One warp.
 template <int DT>
 __global__ void k_serial(SolveArgs a) {
-    if (vload(&a.ctl->desc.mode) != MODE_DONE) serial_step<DT>(a);
+    if (vload(&a.ctl->desc.mode) != MODE_DONE) serial_step<DT>(a, nullptr);
 }
 
 // ---- init / unpack -------------------------------------------------------------
@@ -1081,8 +1112,8 @@ cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, in
 }
 
 cudaError_t launch_serial_step(const SolveArgs &a, cudaStream_t st) {
-    if (a.dtype == DSSSP_F32) k_serial<DSSSP_F32><<<1, 1, 0, st>>>(a);
-    else k_serial<DSSSP_I32><<<1, 1, 0, st>>>(a);
+    if (a.dtype == DSSSP_F32) k_serial<DSSSP_F32><<<1, 32, 0, st>>>(a);
+    else k_serial<DSSSP_I32><<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
