@@ -16,7 +16,8 @@ e2e     the same metric through the public C ABI from pinned HOST buffers: every
 roofline  the solve kernel's algorithmic bytes (per-unit figures below) over
         its CUDA-event time, against the measured HBM copy bandwidth.
 cpu_baseline  the CPU oracle (binary-heap Dijkstra, one source per host core)
-        on a bounded sample of the same sources.
+        on a bounded sample of the same sources; "la_form": the oracle's Fig. 1
+        dense-vector delta-stepping on one thread, one source at Delta 0.1.
 batched / fwd_bwd  (one GPU) batched solves and the forward + adjoint pass against
         the plain per-source solve on the same GPU: 256 sources on a scale-20 R-MAT,
         512 ER graphs of uneven sizes, 32 sources on a scale-20 lognormal R-MAT with
@@ -385,6 +386,13 @@ def main():
         v, used, dt = cpu_oracle_gteps(g, srcs[:k])
         cpu = {"value": v, "unit": "GTEPS", "cores": used, "kind": "oracle",
                "sample": f"{k} of the {len(srcs)} sources, binary-heap Dijkstra one source per thread, {dt:.1f} s"}
+        # the oracle's Fig. 1 linear-algebra form (dense vectors, one thread), one source at Delta 0.1
+        import oracle
+        t0 = time.perf_counter()
+        oracle.delta_la(g.row_ptr, g.col, g.w, srcs[0], 0.1)
+        dla = time.perf_counter() - t0
+        cpu["la_form"] = {"value": g.m / dla / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                          "sample": f"1 source, Delta 0.1, Fig. 1 dense-vector form, {dla:.1f} s"}
 
     if rank == 0:
         line = {
