@@ -12,7 +12,8 @@ value   GTEPS = m * solves / device time, inputs resident in HBM, CUDA events
         cached and timed on its own ("split_ms").
 e2e     the same metric through the public C ABI from pinned HOST buffers: every
         step creates the graph from host CSR, solves all 256 sources and copies
-        every dist/pred array back to pinned host memory.
+        every dist/pred array back to pinned host memory (on a copy stream that
+        overlaps the next solves).
 roofline  the solve kernel's algorithmic bytes (per-unit figures below) over
         its CUDA-event time, against the measured HBM copy bandwidth.
 cpu_baseline  the CPU oracle (binary-heap Dijkstra, one source per host core)
@@ -625,32 +626,49 @@ def profile_driver(args):
 
 
 def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, solo):
-    """Public-API end to end: host CSR -> graph -> 256 solves -> results in pinned host memory."""
+    """Public-API end to end: host CSR -> graph -> 256 solves -> results in pinned host memory.
+
+    Each solve writes one of NB device buffers; its result goes back to pinned host memory on a copy
+    stream while the next solves run, and a buffer is reused only after its copy has finished."""
     rp = torch.from_numpy(g.row_ptr).pin_memory()
     cl = torch.from_numpy(g.col).pin_memory()
     ww = torch.from_numpy(g.w).pin_memory()
     solves = len(deltas) * len(srcs)
-    hd = torch.empty((2, g.n), dtype=torch.float32).pin_memory()
-    hp = torch.empty((2, g.n), dtype=torch.int32).pin_memory()
+    NB = 3
+    hd = torch.empty((NB, g.n), dtype=torch.float32).pin_memory()
+    hp = torch.empty((NB, g.n), dtype=torch.int32).pin_memory()
     stream = torch.cuda.Stream()
+    copy_stream = torch.cuda.Stream()
     steps = max(1, min(args.steps, 2))
 
     def step():
         with torch.cuda.stream(stream):
             h = ds.Graph(rp.numpy(), cl.numpy(), ww.numpy(), stream=stream)
-            dist = torch.empty((2, g.n), dtype=torch.float32, device="cuda")
-            pred = torch.empty((2, g.n), dtype=torch.int32, device="cuda")
-            k = 0
-            for d in deltas:
-                opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, solo_work=solo[d])
-                for s in srcs:
-                    h.solve(s, d, dist=dist[k & 1], pred=pred[k & 1], options=opt, stream=stream)
-                    hd[k & 1].copy_(dist[k & 1], non_blocking=True)
-                    hp[k & 1].copy_(pred[k & 1], non_blocking=True)
-                    k += 1
-            h.sync(stream)
-            stream.synchronize()
-            h.close()
+            dist = torch.empty((NB, g.n), dtype=torch.float32, device="cuda")
+            pred = torch.empty((NB, g.n), dtype=torch.int32, device="cuda")
+        solved = [torch.cuda.Event() for _ in range(NB)]
+        copied = [None] * NB
+        k = 0
+        for d in deltas:
+            opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, solo_work=solo[d])
+            for s in srcs:
+                b = k % NB
+                if copied[b] is not None:
+                    stream.wait_event(copied[b])          # the buffer's previous result is on the host
+                with torch.cuda.stream(stream):
+                    h.solve(s, d, dist=dist[b], pred=pred[b], options=opt, stream=stream)
+                solved[b].record(stream)
+                copy_stream.wait_event(solved[b])
+                with torch.cuda.stream(copy_stream):
+                    hd[b].copy_(dist[b], non_blocking=True)
+                    hp[b].copy_(pred[b], non_blocking=True)
+                    copied[b] = torch.cuda.Event()
+                    copied[b].record(copy_stream)
+                k += 1
+        h.sync(stream)
+        stream.synchronize()
+        copy_stream.synchronize()
+        h.close()
 
     step()
     torch.cuda.synchronize()
