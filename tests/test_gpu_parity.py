@@ -171,6 +171,24 @@ def test_grid_int_deltas(ds, delta):
         assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta} {opt}")
 
 
+@pytest.mark.parametrize("solo_work", [0, 2048, 2**31 - 1])
+def test_window_rebins_with_every_solo_threshold(ds, solo_work):
+    """Re-bins of the bucket window (more than 32 buckets) with phases never solo, solo when small, and always
+    solo (block 0 runs every phase and takes each next view, re-bin thresholds included, from its own serial
+    step); fused and separate heavy passes."""
+    cases = [(W.grid4096(side=200)[0], 0, 100.0), (W.rmat22_unit(scale=15, n_sources=1)[0], None, 0.005)]
+    for g, src, delta in cases:
+        if src is None:
+            src = int(np.argmax(np.diff(g.row_ptr)))
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, src)
+        for flags in (0, 2):
+            d, p, st = gpu_solve(ds, h, src, delta, solo_work=solo_work, flags=flags)
+            assert_same(g, src, d, p, d_ref, p_ref, f"{g.name} solo_work {solo_work} flags {flags}")
+            assert st["rebin_phases"] > 0 and st["buckets"] > 32, st
+        h.close()
+
+
 def test_er_family_small(ds):
     for g, src in W.er_family(count=6, n_lo=1000, n_hi=20000):
         h = ds.Graph(g.row_ptr, g.col, g.w)
