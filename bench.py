@@ -232,6 +232,9 @@ def main():
                     help="profiling driver: one batch of this many scale-20 R-MAT sources at --profile-delta")
     ap.add_argument("--profile-delta", default="0.1",
                     help="comma-separated Deltas, or 'all' for every Delta of the sweep")
+    ap.add_argument("--profile-backward", type=int, default=0,
+                    help="profiling driver: forward with tape + one adjoint pass for this many sources of the "
+                         "scale-20 lognormal R-MAT (Delta 0.36, 8-block teams)")
     ap.add_argument("--no-fuse", action="store_true",
                     help="profiling driver: keep heavy passes and light rounds in separate phases "
                          "(with --mode 1 every phase type is then its own kernel)")
@@ -241,6 +244,9 @@ def main():
         return
     if args.profile_batch:
         profile_batch_driver(args)
+        return
+    if args.profile_backward:
+        profile_backward_driver(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -605,6 +611,29 @@ def profile_batch_driver(args):
                       "max_instance_ms": max(x["ns"] for x in st) / 1e6}), flush=True)
     b.close()
     torch.cuda.synchronize()
+
+
+def profile_backward_driver(args):
+    """Forward (with tape) and one adjoint pass on the scale-20 lognormal R-MAT, for profilers."""
+    import torch
+    import paper_1911_06895_gb300 as ds
+    import graphgen.workloads as W
+    g, srcs, c = W.rmat20_lognormal()
+    srcs = srcs[:args.profile_backward]
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    b = ds.Batch(h, [0.36], srcs, tape=True, options=ds.make_options(team_blocks=8))
+    cs = [torch.from_numpy(c).cuda()] * len(srcs)
+    gw = torch.empty(g.m, dtype=torch.float32, device="cuda")
+    b.run()
+    st = b.sync(stats=True)
+    b.backward(cs, [gw])
+    torch.cuda.synchronize()
+    # algorithmic bytes: per vertex and instance 4 parent + 4 tree arc + 4 c + 8 sum + 8 parent sum + 4 count
+    # + 8 for the tree arc's float64 add; per arc 12 for the float32 output
+    print(json.dumps({"instances": len(st), "n": g.n, "m": g.m, "algorithmic_bytes_backward": 40 * g.n * len(st),
+                      "algorithmic_bytes_grad_out": 12 * g.m,
+                      "grad_abs_sum": float(gw.abs().sum().item())}), flush=True)
+    b.close()
 
 
 def profile_driver(args):
