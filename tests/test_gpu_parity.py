@@ -171,11 +171,11 @@ def test_grid_int_deltas(ds, delta):
         assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta} {opt}")
 
 
-@pytest.mark.parametrize("solo_work", [0, 2048, 2**31 - 1])
+@pytest.mark.parametrize("solo_work", [-1, 2048, 2**31 - 1])
 def test_window_rebins_with_every_solo_threshold(ds, solo_work):
-    """Re-bins of the bucket window (more than 32 buckets) with phases never solo, solo when small, and always
-    solo (block 0 runs every phase and takes each next view, re-bin thresholds included, from its own serial
-    step); fused and separate heavy passes."""
+    """Re-bins of the bucket window (more than 32 buckets) with phases never solo (-1), solo when small (the
+    default), and always solo (block 0 runs every phase and takes each next view, re-bin thresholds included,
+    from its own serial step); fused and separate heavy passes."""
     cases = [(W.grid4096(side=200)[0], 0, 100.0), (W.rmat22_unit(scale=15, n_sources=1)[0], None, 0.005)]
     for g, src, delta in cases:
         if src is None:
