@@ -58,8 +58,8 @@ B_VERTEX, B_ARC, B_FAR, B_INIT_UNPACK = 28, 16, 20, 36
 # DRAM traffic of k_solve_persistent per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum), mean of
 # one launch at each Delta of the sweep (profiles/k_solve_persistent_rmat22_traffic_by_delta.md). It holds only
 # for the kernel source the counters were taken on; any other source reports null.
-TRAFFIC_BYTES_PER_LAUNCH = 3.112e9
-TRAFFIC_SOURCE_SHA256 = "a4310d5701aa303b1b360760aa7fa2766c24e10cf3c99cd47e573648bdd12edc"
+TRAFFIC_BYTES_PER_LAUNCH = 3.104e9
+TRAFFIC_SOURCE_SHA256 = "b614af92c02160f64bd3e03b7982156960ee42754320469267359524b348a07b"
 
 
 def measured_traffic(scale: int):

@@ -53,13 +53,13 @@ using wu::stage_id;
 
 constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 #ifndef DSSSP_ILP
-#define DSSSP_ILP 2
+#define DSSSP_ILP 4
 #endif
 #ifndef DSSSP_MIN_BLOCKS
 #define DSSSP_MIN_BLOCKS 2
 #endif
 constexpr int kIlp = DSSSP_ILP;        // independent 32-arc steps per warp iteration
-constexpr uint32_t kMinSlice = 32u * kIlp;
+constexpr uint32_t kMinSlice = 32u;    // merge-path units of the smallest slice a warp takes
 #ifndef DSSSP_ENTRY_COST
 #define DSSSP_ENTRY_COST 4
 #endif
