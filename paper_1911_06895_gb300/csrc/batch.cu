@@ -49,8 +49,8 @@ using wu::lane_id;
 
 constexpr int kTeamThreads = 512;
 constexpr int kTeamWarps = kTeamThreads / 32;
-constexpr int kTIlp = 2;                    // independent 32-arc steps per warp iteration
-constexpr uint32_t kTMinSlice = 32u * kTIlp;
+constexpr int kTIlp = 4;                    // independent 32-arc steps per warp iteration
+constexpr uint32_t kTMinSlice = 32u;         // merge-path units of the smallest slice a warp takes
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
 enum TMode : uint32_t { T_LIGHT = 0, T_HEAVY = 1, T_SELECT = 2, T_DONE = 3 };
