@@ -19,10 +19,15 @@
  *   - Weights must be non-negative and finite (NaN, +-inf and negative values
  *     are rejected). A float32 -0.0 is stored as +0.0.
  *   - Path sums use the weight type's own addition: float32 adds round to
- *     nearest-even after every arc (an overflow to +inf reads as unreachable);
- *     int32 adds are exact and saturate at INT32_MAX, which reads as unreachable.
- *     Distances are the least fixed point of d[s] = 0, d[v] = min_(u,v) d[u] (+) w;
- *     every relaxation order reaches the same bits.
+ *     nearest-even after every arc; int32 adds are exact. Distances are the
+ *     least fixed point of d[s] = 0, d[v] = min_(u,v) d[u] (+) w; every
+ *     relaxation order reaches the same bits.
+ *   - Overflow (the paper assumes exact reals, Section III; this library's own
+ *     boundary): when some arc (u,v) out of a reached u has a sum d[u] (+) w(u,v)
+ *     that the weight type cannot hold -- an int32 sum >= INT32_MAX (the value
+ *     that marks "unreachable"), or a float32 sum that rounds to +inf -- the solve
+ *     returns DSSSP_ERR_OVERFLOW and writes no output. The condition is taken on
+ *     the final distances, so it does not depend on the relaxation order.
  *   - pred[v] is the smallest u with an arc (u,v) such that d[u] (+) w(u,v) == d[v];
  *     pred[src] = src; unreached vertices get dist = +inf (float32) or
  *     INT32_MAX (int32) and pred = -1.
@@ -56,7 +61,8 @@ typedef enum {
     DSSSP_ERR_OOM = 8,           /* a device allocation failed                                   */
     DSSSP_ERR_UNSUPPORTED = 9,   /* the device or launch shape cannot run this entry point      */
     DSSSP_ERR_TOO_LARGE = 10,    /* the graph exceeds dsssp_solve_noalloc's fixed working memory */
-    DSSSP_ERR_DEGENERATE = 11    /* the predecessor graph has a cycle (zero-weight ties): no gradient */
+    DSSSP_ERR_DEGENERATE = 11,   /* the predecessor graph has a cycle (zero-weight ties): no gradient */
+    DSSSP_ERR_OVERFLOW = 12      /* a path sum out of a reached vertex does not fit the weight type */
 } dsssp_status;
 
 typedef enum { DSSSP_I32 = 0, DSSSP_F32 = 1 } dsssp_dtype;
@@ -169,7 +175,7 @@ dsssp_status dsssp_prepare(dsssp_graph *g, double delta, void *stream);
  * Unless DSSSP_FLAG_ASYNC is set the call waits for the solve and returns its
  * device-side status. Solves on one handle share its workspace: issue them on
  * one stream (or serialize them). Errors: INVALID_ARG, TIMEOUT, NOT_CONVERGED,
- * OOM, CUDA, UNSUPPORTED. */
+ * OVERFLOW, OOM, CUDA, UNSUPPORTED. */
 dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, int32_t *pred,
                          const dsssp_options *opt, dsssp_stats *stats, void *stream);
 
@@ -192,14 +198,17 @@ dsssp_status dsssp_graph_sync(dsssp_graph *g, void *stream);
  *   src, delta  as for dsssp_solve;
  *   dist, pred  DEVICE outputs, n entries each (pred may be NULL), written only
  *               on success.
- * The call validates the CSR on the device and waits for the solve.
- * The first call on a device looks up the device address of the fixed array
- * (once per device, with that device current); make that first call before
- * capturing `stream` into a CUDA graph. Every call uses the same array and
- * clears what it needs first, so calls that overlap on the GPU (for example on
- * two streams) race: serialise them.
+ * The call validates the CSR on the device and waits for the solve (it reads
+ * the result status back to the host), so it cannot run while `stream` is being
+ * captured into a CUDA graph: it then returns DSSSP_ERR_UNSUPPORTED without
+ * touching the stream. The first call on a device looks up the device address
+ * of the fixed array (once per device, with that device current). Every call
+ * uses the same array and clears what it needs first, so calls that overlap on
+ * the GPU (for example on two streams) race: serialise them. A barrier wait
+ * gives up after 2 s without progress (no block arrived and no long row
+ * advanced) and returns DSSSP_ERR_TIMEOUT.
  * Errors: INVALID_ARG, TOO_LARGE, BAD_GRAPH, NEG_WEIGHT, TIMEOUT, NOT_CONVERGED,
- * CUDA, UNSUPPORTED. */
+ * OVERFLOW, CUDA, UNSUPPORTED. */
 dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                                  const void *w, dsssp_dtype dtype, int32_t src, double delta,
                                  void *dist, int32_t *pred, void *stream);
@@ -277,7 +286,8 @@ dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream);
 
 /* Wait for `stream`, then return (and clear) the first device-side status of the runs and
  * backward passes since the last sync (NOT_CONVERGED when an instance hit the phase cap,
- * DEGENERATE from dsssp_backward). stats: NULL or a HOST array of n_inst records, filled
+ * OVERFLOW when a path sum of an instance overflowed -- that instance's outputs are then
+ * not written -- and DEGENERATE from dsssp_backward). stats: NULL or a HOST array of n_inst records, filled
  * from the last run, in the caller's instance order. */
 dsssp_status dsssp_batch_sync(dsssp_batch *b, dsssp_batch_stats *stats, void *stream);
 
@@ -296,8 +306,9 @@ dsssp_status dsssp_solve_batched(dsssp_graph *const *graphs, int32_t n_graphs, c
  * shortest-path tree of instance k, dist_k[v] is the sum of the weights on the tree path
  * from the source to v, so dL/dw(u,v) = sum of c_k[x] over the subtree below v when (u,v) is
  * v's tree arc, and 0 for arcs outside every tree. The tree is taken from the forward run
- * (pred[v] and the input arc that realised dist[v]; among parallel arcs the one met first in
- * the light-then-heavy order of u's row); nothing is re-solved. Subtree sums are accumulated
+ * (the input arc that realised dist[v] -- among all arcs whose sum reaches dist[v], the one
+ * with the smallest input index, whose tail is pred[v]); nothing is re-solved. At such a tie
+ * L has a kink and this rule picks one subgradient. Subtree sums are accumulated
  * leaves first in float64 and rounded to float32 once.
  *   c       HOST array of n_inst DEVICE pointers, float32[n] each (entries of unreached
  *           vertices are ignored);

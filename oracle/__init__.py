@@ -9,10 +9,14 @@ no code with it. It wraps ``oracle.c`` (plain C, built with gcc) through ctypes:
 * ``delta_ms``      delta-stepping in the vertex/edge set form (Fig. 1, right);
 * ``delta_la``      delta-stepping in the linear-algebraic form (Fig. 1, left);
 * ``floyd_warshall_i32``  all-pairs brute force for integer weights;
-* ``check_invariants``    arc inequality / predecessor equality checker;
+* ``check_invariants``    arc inequality, predecessor equality and minimality,
+  realisability (a tight walk from the source reaches every reached vertex) and
+  predecessor chains;
 * ``bucket_index``  the exact bucket function floor(x / Delta) (Section III-B);
 * ``tree_gradient`` dL/dw of L = sum_v c[v] * dist[v] by subtree sums of c over
-  the shortest-path tree (float64), for float32 graphs.
+  the shortest-path tree (float64), for float32 graphs;
+* ``fd_arcs``       central differences of that loss with float64 distances,
+  by local repair of the distances around each perturbed arc.
 
 Every function takes a graph as (row_ptr int64[n+1], col int32[m], w int32|float32[m]).
 """
@@ -70,8 +74,11 @@ def _load():
         lib.or_check_invariants.argtypes = [c.c_int64, vp, vp, vp, c.c_int, c.c_int32, vp, vp]
         lib.or_bucket_index.restype = c.c_int64
         lib.or_bucket_index.argtypes = [c.c_double, c.c_double]
+        lib.or_fd_arcs.restype = c.c_int
+        lib.or_fd_arcs.argtypes = [c.c_int64, vp, vp, vp, vp, vp, vp, c.c_int32, vp, vp, c.c_int64, c.c_double,
+                                   vp, vp]
         lib.or_tree_gradient.restype = c.c_int
-        lib.or_tree_gradient.argtypes = [c.c_int64, vp, vp, vp, c.c_int32, c.c_double, vp, vp, vp, vp]
+        lib.or_tree_gradient.argtypes = [c.c_int64, vp, vp, vp, c.c_int32, vp, vp, vp, vp]
         _lib = lib
     return _lib
 
@@ -93,7 +100,14 @@ def _prep(row_ptr, col, w):
     return row_ptr, col, w, dt
 
 
+class PathOverflow(ValueError):
+    """A path sum out of a reached vertex does not fit the weight type (int32 sum >=
+    INT32_MAX, or a float32 sum that rounds to +inf): the solve has no result."""
+
+
 def _check(rc: int, name: str):
+    if rc == 4:
+        raise PathOverflow(f"{name}: a path sum overflows the weight type")
     if rc != 0:
         raise ValueError(f"{name}: error code {rc} (1 = invalid input, 2 = out of memory)")
 
@@ -199,9 +213,11 @@ class CycleError(ValueError):
     """The predecessor graph has a cycle (zero-weight ties): no gradient."""
 
 
-def tree_gradient(row_ptr, col, w, src, delta, c, dist=None, pred=None, out=None):
+def tree_gradient(row_ptr, col, w, src, c, dist=None, pred=None, out=None):
     """dL/dw (float64[m], input arc order) of L = sum over reached v of c[v] * dist[v]
-    for one source; dist/pred from ``dijkstra`` unless given. Adds into ``out``."""
+    for one source; dist/pred from ``dijkstra`` unless given. Adds into ``out``.
+    The tree arc of v is the arc with the smallest input index among those whose
+    sum reaches dist[v]."""
     lib = _load()
     row_ptr, col, w, dt = _prep(row_ptr, col, w)
     if dt != F32:
@@ -215,7 +231,7 @@ def tree_gradient(row_ptr, col, w, src, delta, c, dist=None, pred=None, out=None
     if c.shape[0] < n:
         raise ValueError("c needs n entries")
     g = out if out is not None else np.zeros(col.shape[0], dtype=np.float64)
-    rc = lib.or_tree_gradient(n, _ptr(row_ptr), _ptr(col), _ptr(w), int(src), float(delta), _ptr(dist),
+    rc = lib.or_tree_gradient(n, _ptr(row_ptr), _ptr(col), _ptr(w), int(src), _ptr(dist),
                               _ptr(pred), _ptr(c), _ptr(g))
     if rc == 3:
         raise CycleError("predecessor graph has a cycle")
@@ -223,11 +239,58 @@ def tree_gradient(row_ptr, col, w, src, delta, c, dist=None, pred=None, out=None
     return g
 
 
-def tree_gradient_many(row_ptr, col, w, sources, delta, cs, threads: int | None = None):
+def tree_gradient_many(row_ptr, col, w, sources, cs, threads: int | None = None):
     """Sum over sources k of tree_gradient(..., sources[k], cs[k]); one source per thread."""
     threads = max(1, min(threads or os.cpu_count() or 1, len(sources)))
     row_ptr, col, w, _ = _prep(row_ptr, col, w)
     with ThreadPoolExecutor(max_workers=threads) as ex:
-        parts = list(ex.map(lambda k: tree_gradient(row_ptr, col, w, sources[k], delta, cs[k]),
+        parts = list(ex.map(lambda k: tree_gradient(row_ptr, col, w, sources[k], cs[k]),
                             range(len(sources))))
     return np.sum(parts, axis=0) if parts else np.zeros(col.shape[0])
+
+
+def reverse_csr(row_ptr, col):
+    """In-arcs of every vertex: (rrow int64[n+1], tails int32[m], input arc index int64[m])."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    n = row_ptr.shape[0] - 1
+    order = np.argsort(col, kind="stable").astype(np.int64)
+    tails = np.repeat(np.arange(n, dtype=np.int32), np.diff(row_ptr))[order]
+    rrow = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(col, minlength=n), out=rrow[1:])
+    return rrow, np.ascontiguousarray(tails, dtype=np.int32), np.ascontiguousarray(order)
+
+
+def fd_arcs(row_ptr, col, w, src, c, arcs, eps=1e-3, rev=None):
+    """Central differences (L(w + eps) - L(w - eps)) / (2 eps) of L = sum over reached x of
+    c[x] * D[x], D the float64 distances from src, for each arc index in ``arcs``.
+    Returns (fd float64[k], kink int32[k]): kink 1 where L is not linear within eps of
+    w[e] (fd is then not the derivative), 2 where w[e] < eps (not tested)."""
+    lib = _load()
+    row_ptr, col, w, dt = _prep(row_ptr, col, w)
+    if dt != F32:
+        raise TypeError("fd_arcs needs float32 weights")
+    n = row_ptr.shape[0] - 1
+    rrow, tails, rarc = rev if rev is not None else reverse_csr(row_ptr, col)
+    c = np.ascontiguousarray(c, dtype=np.float32)
+    arcs = np.ascontiguousarray(arcs, dtype=np.int64)
+    fd = np.zeros(arcs.shape[0], dtype=np.float64)
+    kink = np.zeros(arcs.shape[0], dtype=np.int32)
+    rc = lib.or_fd_arcs(n, _ptr(row_ptr), _ptr(col), _ptr(w), _ptr(rrow), _ptr(tails), _ptr(rarc), int(src),
+                        _ptr(c), _ptr(arcs), arcs.shape[0], float(eps), _ptr(fd), _ptr(kink))
+    _check(rc, "or_fd_arcs")
+    return fd, kink
+
+
+def fd_arcs_many(row_ptr, col, w, sources, cs, arcs, eps=1e-3, threads: int | None = None):
+    """Sum over sources k of fd_arcs(..., sources[k], cs[k], ...); a kink on any source
+    marks the arc. One source per host thread."""
+    threads = max(1, min(threads or os.cpu_count() or 1, len(sources)))
+    row_ptr, col, w, _ = _prep(row_ptr, col, w)
+    rev = reverse_csr(row_ptr, col)
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        parts = list(ex.map(lambda k: fd_arcs(row_ptr, col, w, sources[k], cs[k], arcs, eps, rev),
+                            range(len(sources))))
+    fd = np.sum([p[0] for p in parts], axis=0)
+    kink = np.max([p[1] for p in parts], axis=0)
+    return fd, kink

@@ -12,9 +12,12 @@
  * Section II-A), non-negative weights, one source s. Distances use the weight
  * type's own addition "(+)":
  *   - fp32: IEEE-754 binary32 addition, round-to-nearest-even (a path sum is
- *     rounded after every arc, left to right); an overflow gives +inf;
- *   - int32: exact integer addition saturated at INT32_MAX, which reads as
- *     "unreachable".
+ *     rounded after every arc, left to right);
+ *   - int32: exact integer addition.
+ * A sum the type cannot hold (fp32: rounds to +inf; int32: >= INT32_MAX, the
+ * value that marks "unreachable") is an overflow: when one arc out of a reached
+ * vertex overflows at the fixed point, every solver returns OR_EOVERFLOW and
+ * writes nothing (reading R14).
  * dist is the least fixed point of dist[s] = 0, dist[v] = min over arcs (u,v)
  * of dist[u] (+) w(u,v). Because (+) is monotone and x (+) w >= x for w >= 0,
  * every label-correcting order (Dijkstra, Bellman-Ford, delta-stepping for any
@@ -31,7 +34,8 @@
  *   R4 bucket(x) = floor(x / Delta) evaluated exactly;
  *   R5 a heavy relaxation whose rounded sum lands back in the current bucket
  *      re-opens that bucket (impossible in exact arithmetic; fp32 can do it);
- *   R6 the set form takes the smallest non-empty bucket next (Section III-C).
+ *   R6 the set form takes the smallest non-empty bucket next (Section III-C);
+ *   R14 overflow of a path sum is an error, not "unreachable" (see above).
  *
  * Parity pins: see the test-suite (brute-force walk enumeration, Floyd-Warshall
  * on integer weights, BFS and Manhattan closed forms, prefix sums on paths,
@@ -45,7 +49,7 @@
 #include <string.h>
 
 enum { OR_I32 = 0, OR_F32 = 1 };
-enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2 };
+enum { OR_OK = 0, OR_EINVAL = 1, OR_ENOMEM = 2, OR_ECYCLE = 3, OR_EOVERFLOW = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* values: a distance is held as a double that stores an exact fp32 or int32 */
@@ -65,7 +69,7 @@ static double oplus(int dtype, double d, double w) {
         return (double)r;
     } else {
         double r = d + w;                   /* exact: |values| < 2^53 */
-        if (r >= 2147483647.0) return INFINITY;
+        if (r >= 2147483647.0) return INFINITY;   /* overflow (R14) */
         return r;
     }
 }
@@ -91,6 +95,32 @@ static void pred_from_dist(int64_t n, const int64_t *row_ptr, const int32_t *col
         }
     }
     pred[src] = src;
+}
+
+/* Overflow (reading R14; the paper assumes exact reals, Section III): a solve
+ * is undefined when, at the fixed point, some arc (u,v) out of a reached u has
+ * a sum dist[u] (+) w(u,v) that the weight type cannot hold (int32: >= INT32_MAX;
+ * fp32: rounds to +inf). The condition uses final distances only, so it does
+ * not depend on the relaxation order. Every solver checks it before writing
+ * any output and then returns OR_EOVERFLOW with the outputs untouched. */
+static int overflows(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
+                     int dtype, const double *t) {
+    for (int64_t u = 0; u < n; ++u) {
+        if (isinf(t[u])) continue;
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+            if (isinf(oplus(dtype, t[u], weight_at(dtype, w, e)))) return 1;
+    }
+    (void)col;
+    return 0;
+}
+
+/* the end of every solver: the overflow check, then dist and pred */
+static int finish(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
+                  int dtype, int32_t src, const double *t, void *dist_out, int32_t *pred_out) {
+    if (overflows(n, row_ptr, col, w, dtype, t)) return OR_EOVERFLOW;
+    write_dist(dtype, t, n, dist_out);
+    pred_from_dist(n, row_ptr, col, w, dtype, src, t, pred_out);
+    return OR_OK;
 }
 
 static int check_args(int64_t n, const int64_t *row_ptr, const int32_t *col, const void *w,
@@ -162,10 +192,9 @@ int or_dijkstra(int64_t n, const int64_t *row_ptr, const int32_t *col, const voi
             if (c < t[v]) { t[v] = c; heap_push(h, &sz, (heap_item){c, v}); }
         }
     }
-    write_dist(dtype, t, n, dist_out);
-    pred_from_dist(n, row_ptr, col, w, dtype, src, t, pred_out);
+    rc = finish(n, row_ptr, col, w, dtype, src, t, dist_out, pred_out);
     free(t); free(done); free(h);
-    return OR_OK;
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -191,10 +220,9 @@ int or_bellman_ford(int64_t n, const int64_t *row_ptr, const int32_t *col, const
         }
         if (!changed) break;
     }
-    write_dist(dtype, t, n, dist_out);
-    pred_from_dist(n, row_ptr, col, w, dtype, src, t, pred_out);
+    rc = finish(n, row_ptr, col, w, dtype, src, t, dist_out, pred_out);
     free(t);
-    return OR_OK;
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -418,11 +446,7 @@ int or_delta_ms(int64_t n, const int64_t *row_ptr, const int32_t *col, const voi
             if (!reopened) break;
         }
     }
-    {
-        double *t = st.tent;
-        write_dist(dtype, t, n, dist_out);
-        pred_from_dist(n, row_ptr, col, w, dtype, src, t, pred_out);
-    }
+    rc = finish(n, row_ptr, col, w, dtype, src, st.tent, dist_out, pred_out);
 out:
     if (trace_len) *trace_len = tb.overflow ? -tb.len : tb.len;
     free(st.tent); free(st.bucket_of); free(st.heap.h); free(bi); free(S); free(inS); free(req);
@@ -512,8 +536,7 @@ int or_delta_la(int64_t n, const int64_t *row_ptr, const int32_t *col, const voi
         }
         i = i + 1;                                                       /* i = i + 1 */
     }
-    write_dist(dtype, t, n, dist_out);
-    pred_from_dist(n, row_ptr, col, w, dtype, src, t, pred_out);
+    rc = finish(n, row_ptr, col, w, dtype, src, t, dist_out, pred_out);
 out:
     if (trace_len) *trace_len = tb.overflow ? -tb.len : tb.len;
     free(t); free(t_req); free(t_b); free(S);
@@ -525,15 +548,28 @@ out:
 /*   (a) dist[v] <= dist[u] (+) w for every arc (u,v) with u reached;        */
 /*   (b) dist[pred[v]] (+) w(pred[v], v) == dist[v] for every reached v != s; */
 /*   (c) pred[v] is the smallest such u;  (d) dist[s] == 0, pred[s] == s;     */
-/*   (e) unreached v (dist = INF) has pred -1.                                */
+/*   (e) unreached v (dist = INF) has pred -1;                                */
+/*   (f) every reached v is realised: a walk from s along tight arcs (arcs    */
+/*       with dist[u] (+) w == dist[v]) reaches it. With (a) this pins the     */
+/*       least fixed point: (f) gives dist[v] = the rounded sum of one walk,   */
+/*       (a) and the monotonicity of (+) give dist[v] <= every walk's sum.     */
+/*       Without (f) a labelling that is too small on a cycle of zero-effect  */
+/*       arcs (w = 0, or an fp32 w absorbed by a large dist) would pass (a)-(e);*/
+/*   (g) following pred from a reached v reaches s, or ends in a cycle whose  */
+/*       vertices all have the same distance (a tie the smallest-id rule can  */
+/*       close through zero-effect arcs; legal only together with (f)); a     */
+/*       chain that leaves the reached set or runs longer than n is counted.  */
 
 int64_t or_check_invariants(int64_t n, const int64_t *row_ptr, const int32_t *col,
                             const void *w, int dtype, int32_t src, const void *dist,
                             const int32_t *pred) {
+    if (n <= 0 || src < 0 || src >= n) return -1;
     int64_t bad = 0;
     double *t = (double *)malloc((size_t)n * sizeof(double));
     int32_t *best = (int32_t *)malloc((size_t)n * sizeof(int32_t));
-    if (!t || !best) { free(t); free(best); return -1; }
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint8_t *state = (uint8_t *)calloc((size_t)n, 1);
+    if (!t || !best || !queue || !state) { free(t); free(best); free(queue); free(state); return -1; }
     for (int64_t v = 0; v < n; ++v) {
         if (dtype == OR_F32) { float x = ((const float *)dist)[v]; t[v] = isinf(x) ? INFINITY : (double)x; }
         else { int32_t x = ((const int32_t *)dist)[v]; t[v] = x == INT32_MAX ? INFINITY : (double)x; }
@@ -555,7 +591,54 @@ int64_t or_check_invariants(int64_t n, const int64_t *row_ptr, const int32_t *co
         if (pred[v] < 0 || pred[v] >= n) { ++bad; continue; }
         if (best[v] != pred[v]) ++bad;                                               /* (b),(c) */
     }
-    free(t); free(best);
+    /* (f) breadth-first search from s over tight arcs (state 1 = visited) */
+    if (t[src] == 0.0) {
+        int64_t head = 0, tail = 0;
+        queue[tail++] = src;
+        state[src] = 1;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                int32_t v = col[e];
+                if (state[v]) continue;
+                double c = oplus(dtype, t[u], weight_at(dtype, w, e));
+                if (!isinf(c) && c == t[v]) { state[v] = 1; queue[tail++] = v; }
+            }
+        }
+    }
+    for (int64_t v = 0; v < n; ++v) if (!isinf(t[v]) && !state[v]) ++bad;
+    /* (g) pred walks. state: 0/1 not yet classified, 2 on the current walk,
+       3 reaches s, 4 ends in an equal-distance cycle, 5 broken chain */
+    for (int64_t v = 0; v < n; ++v) if (state[v] == 1) state[v] = 0;
+    state[src] = 3;
+    for (int64_t v0 = 0; v0 < n; ++v0) {
+        if (isinf(t[v0]) || state[v0] >= 3) continue;
+        int64_t len = 0;
+        int32_t x = (int32_t)v0;
+        uint8_t verdict = 5;
+        for (;;) {
+            if (state[x] >= 3) { verdict = state[x]; break; }
+            if (state[x] == 2) {                  /* a cycle closes at x: equal distances? */
+                verdict = 4;
+                int32_t y = x;
+                int64_t k = 0;
+                do {
+                    int32_t py = pred[y];
+                    if (t[py] != t[y]) verdict = 5;
+                    y = py;
+                } while (y != x && ++k <= n);
+                break;
+            }
+            state[x] = 2;
+            queue[len++] = x;
+            int32_t px = pred[x];
+            if (px < 0 || px >= n || isinf(t[px]) || len > n) { verdict = 5; break; }
+            x = px;
+        }
+        for (int64_t k = 0; k < len; ++k) state[queue[k]] = verdict;
+        if (verdict == 5) bad += len;
+    }
+    free(t); free(best); free(queue); free(state);
     return bad;
 }
 
@@ -567,17 +650,18 @@ int64_t or_check_invariants(int64_t n, const int64_t *row_ptr, const int32_t *co
 /* by eps raises dist[x] by eps for every x in the subtree below v (as long  */
 /* as the tree stays the same): dL/dw(tree arc of v) = sum of c over that     */
 /* subtree, and 0 for arcs outside the tree.                                  */
-/* The tree arc of v is an arc (pred[v], v) whose sum reaches dist[v]; among  */
-/* parallel arcs that do, the first in pred[v]'s light-then-heavy order       */
-/* (light: w <= Delta, Section III-A), input order within each group.         */
+/* The tree arc of v (reading R11) is, among all arcs (u,v) whose sum        */
+/* dist[u] (+) w reaches dist[v], the one with the smallest input index.     */
+/* Input arcs are stored row by row, so its tail is the smallest such u,     */
+/* which is pred[v]; between parallel arcs of that row the earlier one wins. */
+/* (At such a tie L has a kink -- the two arcs' one-sided derivatives        */
+/* differ -- and this picks one subgradient by a rule of the input alone.)   */
 /* Subtree sums are accumulated in double by an explicit post-order walk.    */
 /* grad (m entries) is ADDED to. Returns 3 when the predecessor graph has a   */
 /* cycle (zero-weight ties), where the gradient is undefined.                 */
 
-enum { OR_ECYCLE = 3 };
-
 int or_tree_gradient(int64_t n, const int64_t *row_ptr, const int32_t *col, const float *w,
-                     int32_t src, double delta, const float *dist, const int32_t *pred,
+                     int32_t src, const float *dist, const int32_t *pred,
                      const float *c, double *grad) {
     if (n <= 0 || src < 0 || src >= n) return OR_EINVAL;
     int64_t *tree = (int64_t *)malloc((size_t)n * sizeof(int64_t));
@@ -600,13 +684,8 @@ int or_tree_gradient(int64_t n, const int64_t *row_ptr, const int32_t *col, cons
         if (v == src) continue;
         int32_t u = pred[v];
         if (u < 0 || u >= n) { rc = OR_EINVAL; goto out; }
-        for (int pass = 0; pass < 2 && tree[v] < 0; ++pass) {        /* light, then heavy */
-            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
-                if (col[e] != v) continue;
-                int light = (double)w[e] <= delta;
-                if ((pass == 0) != light) continue;
-                if (oplus(OR_F32, (double)dist[u], (double)w[e]) == (double)dist[v]) { tree[v] = e; break; }
-            }
+        for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {        /* first in input order */
+            if (col[e] == v && oplus(OR_F32, (double)dist[u], (double)w[e]) == (double)dist[v]) { tree[v] = e; break; }
         }
         if (tree[v] < 0) { rc = OR_EINVAL; goto out; }                /* pred does not realise dist */
     }
@@ -639,5 +718,217 @@ int or_tree_gradient(int64_t n, const int64_t *row_ptr, const int32_t *col, cons
     }
 out:
     free(tree); free(head); free(kids); free(stack); free(next); free(sum);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Central differences of the loss in float64: a check of the gradient, not  */
+/* a step of the method. For one source and float32 weights w (read as exact */
+/* doubles, summed in double), L(w) = sum over reached x of c[x] * D[x] with  */
+/* D the float64 shortest-path distances. For every listed arc e,            */
+/*   fd = (L(w + eps 1_e) - L(w - eps 1_e)) / (2 eps),                        */
+/* with D recomputed only where it can change:                               */
+/*  - lowering w_e, e = (u,v), can only lower distances reached through e: a  */
+/*    Dijkstra seeded at v with D[u] + w_e - eps finds them;                  */
+/*  - raising w_e changes nothing unless e is v's tree arc; then exactly the  */
+/*    tree below v may rise: its vertices are solved again from their in-arcs */
+/*    out of the rest of the graph (whose distances stay), inside the subtree. */
+/* The tree arc of v is the smallest input index among arcs whose float64 sum */
+/* equals D[v]. L is piecewise linear in w_e; kink[j] = 1 when some vertex's   */
+/* distance is not linear on [w_e - eps, w_e + eps] (it moves by a different  */
+/* amount on the two sides), where fd is not the derivative; kink[j] = 2 when */
+/* w_e < eps (not tested). The reverse CSR (rrow, rtail, rarc: in-arcs of     */
+/* every vertex, their tails and input indices) is passed in.                */
+
+typedef struct {
+    int64_t n;
+    const int64_t *rp; const int32_t *col; const double *w;
+    const int64_t *rrp; const int32_t *rtail; const int64_t *rarc;
+    double *D;            /* float64 distances at w                          */
+    int64_t *tree;        /* tree arc of every reached v != src, else -1     */
+    int64_t *kp;          /* children of every vertex in the tree (CSR)       */
+    int32_t *kids;
+    double *Dn;           /* perturbed distances of the touched vertices      */
+    uint8_t *mark;        /* 1 touched, 2 in the re-solved subtree            */
+    int32_t *touched; int64_t nt;
+    heap_item *h; int64_t hcap;
+    int32_t *stack;
+    double *dplus;        /* per-vertex rise under +eps (0 when untouched)     */
+    int32_t *plist; int64_t np;
+} fd_state;
+
+static void fd_touch(fd_state *s, int32_t x, uint8_t how) {
+    if (!s->mark[x]) { s->touched[s->nt++] = x; s->Dn[x] = s->D[x]; }
+    s->mark[x] = how;
+}
+
+static void fd_reset(fd_state *s) {
+    for (int64_t k = 0; k < s->nt; ++k) s->mark[s->touched[k]] = 0;
+    s->nt = 0;
+}
+
+/* lower w_e to wnew: Dn on the touched vertices */
+static void fd_lower(fd_state *s, int64_t e, int32_t u, int32_t v, double wnew) {
+    if (isinf(s->D[u])) return;
+    double cand = s->D[u] + wnew;
+    if (!(cand < s->D[v])) return;
+    int64_t sz = 0;
+    fd_touch(s, v, 1);
+    s->Dn[v] = cand;
+    heap_push(s->h, &sz, (heap_item){cand, v});
+    while (sz > 0) {
+        heap_item it = heap_pop(s->h, &sz);
+        int32_t x = it.v;
+        if (it.key != s->Dn[x]) continue;
+        for (int64_t a = s->rp[x]; a < s->rp[x + 1]; ++a) {
+            int32_t y = s->col[a];
+            double c = s->Dn[x] + (a == e ? wnew : s->w[a]);
+            double cur = s->mark[y] ? s->Dn[y] : s->D[y];
+            if (c < cur) {
+                fd_touch(s, y, 1);
+                s->Dn[y] = c;
+                if (sz < s->hcap) heap_push(s->h, &sz, (heap_item){c, y});
+            }
+        }
+    }
+}
+
+/* raise w_e to wnew: Dn on the subtree below v when e is v's tree arc */
+static void fd_raise(fd_state *s, int64_t e, int32_t v, double wnew) {
+    if (s->tree[v] != e) return;
+    int64_t top = 0, first = s->nt;
+    s->stack[top++] = v;
+    while (top > 0) {                                  /* the subtree, marked 2 */
+        int32_t x = s->stack[--top];
+        fd_touch(s, x, 2);
+        s->Dn[x] = INFINITY;
+        for (int64_t k = s->kp[x]; k < s->kp[x + 1]; ++k) s->stack[top++] = s->kids[k];
+    }
+    int64_t sz = 0;
+    for (int64_t k = first; k < s->nt; ++k) {          /* entries from outside */
+        int32_t x = s->touched[k];
+        for (int64_t r = s->rrp[x]; r < s->rrp[x + 1]; ++r) {
+            int32_t y = s->rtail[r];
+            if (s->mark[y] == 2 || isinf(s->D[y])) continue;
+            int64_t a = s->rarc[r];
+            double c = s->D[y] + (a == e ? wnew : s->w[a]);
+            if (c < s->Dn[x]) s->Dn[x] = c;
+        }
+        if (!isinf(s->Dn[x])) heap_push(s->h, &sz, (heap_item){s->Dn[x], x});
+    }
+    while (sz > 0) {                                   /* Dijkstra inside the subtree */
+        heap_item it = heap_pop(s->h, &sz);
+        int32_t x = it.v;
+        if (it.key != s->Dn[x]) continue;
+        for (int64_t a = s->rp[x]; a < s->rp[x + 1]; ++a) {
+            int32_t y = s->col[a];
+            if (s->mark[y] != 2) continue;
+            double c = s->Dn[x] + (a == e ? wnew : s->w[a]);
+            if (c < s->Dn[y]) {
+                s->Dn[y] = c;
+                if (sz < s->hcap) heap_push(s->h, &sz, (heap_item){c, y});
+            }
+        }
+    }
+}
+
+int or_fd_arcs(int64_t n, const int64_t *row_ptr, const int32_t *col, const float *wf,
+               const int64_t *rrow, const int32_t *rtail, const int64_t *rarc,
+               int32_t src, const float *c, const int64_t *arcs, int64_t k, double eps,
+               double *fd, int32_t *kink) {
+    if (n <= 0 || src < 0 || src >= n || !(eps > 0.0)) return OR_EINVAL;
+    const int64_t m = row_ptr[n];
+    fd_state s;
+    memset(&s, 0, sizeof s);
+    s.n = n; s.rp = row_ptr; s.col = col; s.rrp = rrow; s.rtail = rtail; s.rarc = rarc;
+    double *w = (double *)malloc((size_t)(m ? m : 1) * sizeof(double));
+    int32_t *tail = (int32_t *)malloc((size_t)(m ? m : 1) * sizeof(int32_t));
+    s.D = (double *)malloc((size_t)n * sizeof(double));
+    s.tree = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    s.kp = (int64_t *)calloc((size_t)(n + 1), sizeof(int64_t));
+    s.kids = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    s.Dn = (double *)malloc((size_t)n * sizeof(double));
+    s.mark = (uint8_t *)calloc((size_t)n, 1);
+    s.touched = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    s.hcap = m + n + 1;
+    s.h = (heap_item *)malloc((size_t)s.hcap * sizeof(heap_item));
+    s.stack = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    s.dplus = (double *)calloc((size_t)n, sizeof(double));
+    s.plist = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    uint8_t *done = (uint8_t *)calloc((size_t)n, 1);
+    int64_t *next = (int64_t *)malloc((size_t)(n + 1) * sizeof(int64_t));
+    int rc = OR_OK;
+    if (!w || !tail || !s.D || !s.tree || !s.kp || !s.kids || !s.Dn || !s.mark || !s.touched || !s.h ||
+        !s.stack || !s.dplus || !s.plist || !done || !next) { rc = OR_ENOMEM; goto out; }
+    for (int64_t e = 0; e < m; ++e) w[e] = (double)wf[e];
+    for (int64_t u = 0; u < n; ++u) for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) tail[e] = (int32_t)u;
+    s.w = w;
+    /* float64 Dijkstra */
+    for (int64_t v = 0; v < n; ++v) { s.D[v] = INFINITY; s.tree[v] = -1; }
+    s.D[src] = 0.0;
+    {
+        int64_t sz = 0;
+        heap_push(s.h, &sz, (heap_item){0.0, src});
+        while (sz > 0) {
+            heap_item it = heap_pop(s.h, &sz);
+            int32_t u = it.v;
+            if (done[u] || it.key != s.D[u]) continue;
+            done[u] = 1;
+            for (int64_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                double cnd = s.D[u] + w[e];
+                if (cnd < s.D[col[e]]) { s.D[col[e]] = cnd; heap_push(s.h, &sz, (heap_item){cnd, col[e]}); }
+            }
+        }
+    }
+    /* tree arcs (smallest input index realising D[v]) and the children lists */
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t u = tail[e], v = col[e];
+        if (v == src || isinf(s.D[u]) || s.tree[v] >= 0) continue;
+        if (s.D[u] + w[e] == s.D[v]) s.tree[v] = e;
+    }
+    for (int64_t v = 0; v < n; ++v) if (s.tree[v] >= 0) s.kp[tail[s.tree[v]] + 1]++;
+    for (int64_t v = 0; v < n; ++v) s.kp[v + 1] += s.kp[v];
+    for (int64_t v = 0; v <= n; ++v) next[v] = s.kp[v];
+    for (int64_t v = 0; v < n; ++v) if (s.tree[v] >= 0) s.kids[next[tail[s.tree[v]]]++] = (int32_t)v;
+    for (int64_t j = 0; j < k; ++j) {
+        int64_t e = arcs[j];
+        fd[j] = 0.0;
+        kink[j] = 0;
+        if (e < 0 || e >= m) { rc = OR_EINVAL; goto out; }
+        if (w[e] < eps) { kink[j] = 2; continue; }
+        int32_t u = tail[e], v = col[e];
+        double dl = 0.0;
+        /* +eps */
+        fd_raise(&s, e, v, w[e] + eps);
+        s.np = 0;
+        for (int64_t t = 0; t < s.nt; ++t) {
+            int32_t x = s.touched[t];
+            double d = s.Dn[x] - s.D[x];
+            dl += (double)c[x] * d;
+            s.dplus[x] = d;
+            s.plist[s.np++] = x;
+        }
+        fd_reset(&s);
+        /* -eps */
+        fd_lower(&s, e, u, v, w[e] - eps);
+        for (int64_t t = 0; t < s.nt; ++t) {
+            int32_t x = s.touched[t];
+            double d = s.D[x] - s.Dn[x];
+            dl += (double)c[x] * d;
+            if (fabs(d - s.dplus[x]) > 1e-9) kink[j] = 1;
+            s.dplus[x] = INFINITY;                      /* compared */
+        }
+        for (int64_t t = 0; t < s.np; ++t) {             /* rose under +eps, unmoved under -eps */
+            int32_t x = s.plist[t];
+            if (!isinf(s.dplus[x]) && fabs(s.dplus[x]) > 1e-9) kink[j] = 1;
+            s.dplus[x] = 0.0;
+        }
+        for (int64_t t = 0; t < s.nt; ++t) s.dplus[s.touched[t]] = 0.0;
+        fd_reset(&s);
+        fd[j] = dl / (2.0 * eps);
+    }
+out:
+    free(w); free(tail); free(s.D); free(s.tree); free(s.kp); free(s.kids); free(s.Dn); free(s.mark);
+    free(s.touched); free(s.h); free(s.stack); free(s.dplus); free(s.plist); free(done); free(next);
     return rc;
 }

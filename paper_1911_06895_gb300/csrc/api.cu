@@ -165,6 +165,7 @@ const char *dsssp_status_string(dsssp_status s) {
     case DSSSP_ERR_UNSUPPORTED: return "unsupported device or launch shape";
     case DSSSP_ERR_TOO_LARGE: return "graph exceeds the fixed working memory of the no-allocation solve";
     case DSSSP_ERR_DEGENERATE: return "predecessor graph has a cycle (zero-weight ties): gradient undefined";
+    case DSSSP_ERR_OVERFLOW: return "a path sum overflows the weight type";
     }
     return "unknown status";
 }
@@ -336,6 +337,7 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
             DSSSP_TRY(launch_phase_stepped(a, mode, grid, opt.block_size, st));
             DSSSP_TRY(launch_serial_step(a, st));
         }
+        DSSSP_TRY(launch_verify_overflow(a, grid, opt.block_size, st));
     }
     DSSSP_TRY(launch_unpack(a, dist, pred, st));
     k_sticky<<<1, 1, 0, st>>>(g->ctl, g->sticky);

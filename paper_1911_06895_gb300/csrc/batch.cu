@@ -18,9 +18,10 @@
 // A team's phases are separated by block barriers only, so a phase costs a few
 // dependent memory round trips; the other teams keep the memory system busy.
 // The low word of packed[] is the predecessor vertex, or -- with a tape -- the
-// split position of the arc that realised the distance. Rows occupy ascending
-// split positions, so the minimum over (key, position) selects the same
-// predecessor as the minimum over (key, vertex).
+// input index of the arc that realised the distance. Input arcs are stored row
+// by row, so the minimum over (key, input index) selects the same predecessor
+// as the minimum over (key, vertex), and among parallel arcs of that row the
+// one with the smallest input index (the tree-arc rule of the gradient).
 //
 // Adjoint (k_backward). With L = sum_v c[v] * d[v] and d[v] the sum of the
 // tree-path weights, dL/dw(e) for the tree arc e = (pred[v], v) is the sum of c
@@ -64,7 +65,8 @@ struct BGraphDev {
     const uint4 *vinfo;        // n: (light begin, light end = heavy begin, heavy end, 0)
     const uint2 *arcs;         // m: (head, weight bits), light first per row
     const uint32_t *perm;      // m: split position -> input arc index
-    const uint32_t *tail;      // m: split position -> row (tape only)
+    const uint32_t *tail;      // m: arc position -> row (tape only; a row covers the same
+                               //    positions in the input and in the split order)
     double delta;
     uint32_t n, m;
 };
@@ -117,6 +119,7 @@ struct Ph {
     uint32_t count, arcs;           // its entries and arcs
     uint32_t *nstamp, *sstamp, *fflag;
     uint32_t *far_min, *next_min;   // team reductions
+    uint32_t *ovf;                  // team flag: a relaxation met a sum the weight type cannot hold
     unsigned long long *improve, *a_light, *a_heavy;
     uint32_t T, T_lo, pstamp, sst, fst, mode;
 };
@@ -134,6 +137,8 @@ struct TeamShared {
     uint32_t nX[2];
     uint32_t far_min;                        // <= every key of a live far entry
     uint32_t next_min;                       // SELECT: smallest key kept
+    uint32_t ovf;                            // a relaxation met a sum the weight type cannot hold
+    uint32_t ovf_bad;                        // the final check confirmed an overflow
     uint32_t mode, cur, scur, xcur, pstamp, sst, T, T_lo, fst, gen, inst;
     uint32_t gen_seen;                       // every block: the leader's generator at instance start
 };
@@ -154,6 +159,7 @@ struct TStage {
 struct Team {
     const uint4 *vinfo;
     const uint2 *arcs;
+    const uint32_t *perm;      // split position -> input arc index (tape)
     unsigned long long *packed;
     uint32_t n, m;
 };
@@ -253,6 +259,7 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
     const uint32_t lane = lane_id();
     const uint32_t *offs = reinterpret_cast<const uint32_t *>(list) + 1;   // offs[2 * j]
     uint32_t nf = 0, ns = 0, nx = 0, nrec = 0;
+    bool ovf = false;                       // a sum the weight type cannot hold
     // merge-path over entries and arcs together (an entry weighs kTEntryCost arcs);
     // the first arc of entry i sits at (i + 1) * kTEntryCost + offs[i]
     const unsigned long long W = (unsigned long long)count * kTEntryCost + E;
@@ -365,8 +372,16 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
             #pragma unroll
             for (int k = 0; k < kTIlp; ++k) {
                 ck[k] = ok[k] ? key_add<DT>(okey[k], arc[k].y) : inf_key<DT>();
-                cand[k] = ((unsigned long long)ck[k] << 32) | (TAPE ? ai[k] : ov[k]);
+                ovf |= ok[k] && ck[k] >= inf_key<DT>();
                 cur[k] = ck[k] < inf_key<DT>() ? __ldcg(t.packed + arc[k].x) : 0ull;
+            }
+            // with a tape the low word is the arc's input index, read only for a
+            // request that can win or tie on the key
+            #pragma unroll
+            for (int k = 0; k < kTIlp; ++k) {
+                uint32_t low = ov[k];
+                if (TAPE) low = (ck[k] < inf_key<DT>() && ck[k] <= (uint32_t)(cur[k] >> 32)) ? __ldcs(t.perm + ai[k]) : NONE;
+                cand[k] = ((unsigned long long)ck[k] << 32) | low;
             }
             // packed[v] only decreases: a value read earlier bounds it, so the
             // atomic is skipped when the request cannot win (old = 0: no win)
@@ -392,6 +407,7 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
             }
         }
         if (lane == 0) relaxed += e1 - e0;
+        if (__any_sync(FULL, ovf) && lane == 0) *ph.ovf = 1u;
     }
     if (nrec) {
         __syncwarp();
@@ -532,6 +548,7 @@ __device__ __noinline__ void build_view(Ph &ph, TeamShared *L, const BatchArgs &
     ph.fflag = a.ws.fflag + off;
     ph.far_min = &L->far_min;
     ph.next_min = &L->next_min;
+    ph.ovf = &L->ovf;
     ph.improve = &L->improve;
     ph.a_light = &L->a_light;
     ph.a_heavy = &L->a_heavy;
@@ -581,6 +598,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
         if (ii >= a.n_inst) break;
         t.vinfo = s.G.vinfo;
         t.arcs = s.G.arcs;
+        t.perm = s.G.perm;
         t.n = s.G.n;
         t.m = s.G.m;
         // stamps restart from 1 before the leader's generator could wrap
@@ -605,6 +623,8 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             s.nX[0] = s.nX[1] = 0u;
             s.far_min = inf_key<DT>();
             s.next_min = inf_key<DT>();
+            s.ovf = 0u;
+            s.ovf_bad = 0u;
             s.cur = s.scur = s.xcur = 0u;
             s.fst = ++s.gen;
             s.sst = ++s.gen;
@@ -658,8 +678,36 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             if (tid == 0) build_view<DT>(ph, cl.map_shared_rank(&s, 0), a, off);
             __syncthreads();
         }
+        // Overflow (reading R14): when a relaxation met a sum the weight type
+        // cannot hold, every arc of every reached vertex is tested again with its
+        // final distance (one warp per vertex); a confirmed overflow fails the
+        // batch with DSSSP_ERR_OVERFLOW and leaves this instance's outputs alone.
+        bool write_out = true;
+        if (tid == 0) s.ovf = cl.map_shared_rank(&s, 0)->ovf;   // same value in every block of the team
+        __syncthreads();
+        if (s.ovf) {
+            uint32_t *bad_flag = &cl.map_shared_rank(&s, 0)->ovf_bad;
+            const uint32_t lane = lane_id();
+            for (uint32_t v = team_warp(); v < t.n; v += team_warps()) {
+                const uint32_t k = (uint32_t)(__ldcg(t.packed + v) >> 32);
+                if (k >= inf_key<DT>()) continue;
+                const uint4 vi = t.vinfo[v];
+                bool bad = false;
+                for (uint32_t e = vi.x + lane; e < vi.z && e < t.m; e += 32u)
+                    bad |= key_add<DT>(k, __ldcg(t.arcs + e).y) >= inf_key<DT>();
+                if (__any_sync(FULL, bad)) {
+                    if (lane == 0) *bad_flag = 1u;
+                    break;
+                }
+            }
+            cl.sync();
+            if (cl.map_shared_rank(&s, 0)->ovf_bad) {
+                write_out = false;
+                if (leader && tid == 0) atomicCAS(a.err, 0, (int)DSSSP_ERR_OVERFLOW);
+            }
+        }
         // unpack: dist = key bits; pred from the low word (tape: via the arc's row)
-        {
+        if (write_out) {
             const BInstDev &I = s.I;
             const BGraphDev &G = s.G;
             const uint32_t src = I.src;
@@ -671,7 +719,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
                 uint32_t pr = NONE, tree = NONE;
                 if (reached) {
                     if (v == src) pr = src;
-                    else if (TAPE) { pr = low < t.m ? G.tail[low] : NONE; tree = low < t.m ? G.perm[low] : NONE; }
+                    else if (TAPE) { pr = low < t.m ? G.tail[low] : NONE; tree = low < t.m ? low : NONE; }
                     else pr = low;
                 }
                 dist[v] = key;

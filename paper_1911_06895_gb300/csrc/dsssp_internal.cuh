@@ -165,7 +165,7 @@ struct Ctl {
     unsigned int bar_count;
     unsigned int bar_gen;
     int32_t err;            // first dsssp_status != OK
-    uint32_t pad0;
+    uint32_t ovf;           // 1: a relaxation met a sum the weight type cannot hold (checked at the end)
     uint64_t t_first;       // %globaltimer of the first arrival at the current barrier
     uint32_t pad1[26];
     PhaseDesc desc;
@@ -235,6 +235,7 @@ cudaError_t solve_occupancy(int block, int *blocks_per_sm);
 cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, int block,
                                  cudaStream_t st);
 cudaError_t launch_serial_step(const SolveArgs &a, cudaStream_t st);
+cudaError_t launch_verify_overflow(const SolveArgs &a, int grid, int block, cudaStream_t st);
 cudaError_t launch_unpack(const SolveArgs &a, void *dist, int32_t *pred, cudaStream_t st);
 
 }  // namespace dsssp

@@ -39,8 +39,9 @@ struct NaCtl {
     uint32_t next_count;      // vertices stamped for the next light round
     uint32_t far_min;         // lower bound on the keys of far (later-bucket) vertices
     uint32_t far_count;       // vertices on the far pile
-    uint32_t pad;
+    uint32_t ovf;             // 1: a relaxation met a sum the weight type cannot hold
     long long phases;
+    unsigned long long progress;   // bumped as rows are scanned: a waiting block's clock restarts on it
 };
 
 struct NaScratch {
@@ -74,6 +75,9 @@ __device__ __forceinline__ uint32_t na_add(uint32_t dkey, uint32_t wbits) {
 }
 
 // Grid barrier with a bounded wait; the last arrival runs `serial` (one thread).
+// The wait gives up after timeout_ns without progress: the clock restarts
+// whenever another block arrives or a warp reports scanned arcs, so one warp
+// scanning a very long row keeps the others waiting as long as it advances.
 template <typename F>
 __device__ bool na_barrier(NaCtl *c, uint32_t nblocks, int64_t timeout_ns, F serial) {
     __shared__ int ok;
@@ -88,13 +92,24 @@ __device__ bool na_barrier(NaCtl *c, uint32_t nblocks, int64_t timeout_ns, F ser
             __threadfence();
             atomicExch(&c->bar_gen, gen + 1u);
         } else {
-            const uint64_t t0 = na_timer();
+            uint64_t t0 = na_timer();
+            unsigned seen_count = na_vload(&c->bar_count);
+            unsigned long long seen_prog = na_vload(&c->progress);
             while (na_vload(&c->bar_gen) == gen) {
                 if (na_vload(&c->err) != 0) break;
-                if ((int64_t)(na_timer() - t0) > timeout_ns) {
+                const uint64_t now = na_timer();
+                const unsigned cnt = na_vload(&c->bar_count);
+                const unsigned long long prog = na_vload(&c->progress);
+                if (cnt != seen_count || prog != seen_prog) {
+                    seen_count = cnt;
+                    seen_prog = prog;
+                    t0 = now;
+                }
+                if ((int64_t)(now - t0) > timeout_ns) {
                     atomicCAS(&c->err, 0, (int)DSSSP_ERR_TIMEOUT);
                     break;
                 }
+                __nanosleep(256);
             }
             __threadfence();
         }
@@ -164,13 +179,16 @@ __device__ void na_relax_row(const NaArgs &a, uint32_t u, uint32_t du, bool ligh
     NaScratch *s = a.s;
     const uint32_t lane = threadIdx.x & 31u;
     const int64_t b = a.row_ptr[u], e = a.row_ptr[u + 1];
+    bool ovf = false;
     for (int64_t k = b + lane; k < e; k += 32) {
+        // a long row tells waiting blocks that it advances (every 64 x 32 arcs)
+        if (lane == 0 && ((k - b) & 2047) == 2047 - 31) atomicAdd(&s->ctl.progress, 1ull);
         uint32_t w = a.wbits[k];
         if (DT == DSSSP_F32 && w == 0x80000000u) w = 0u;            // -0.0 is +0.0
         if ((w <= a.light_max) != light) continue;                   // A_L o t_Bi  /  A_H o S
         const uint32_t v = (uint32_t)a.col[k];
         const uint32_t ck = na_add<DT>(du, w);
-        if (ck >= na_inf<DT>()) continue;
+        if (ck >= na_inf<DT>()) { ovf = true; continue; }           // checked again at the end
         const unsigned long long cand = ((unsigned long long)ck << 32) | u;
         if (cand >= __ldcg(&s->packed[v])) continue;
         const unsigned long long old = atomicMin(&s->packed[v], cand);
@@ -182,6 +200,7 @@ __device__ void na_relax_row(const NaArgs &a, uint32_t u, uint32_t du, bool ligh
             if (atomicExch(&s->far[v], 1u) == 0u) ++farn;
         }
     }
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) s->ctl.ovf = 1u;
 }
 
 template <int DT>
@@ -286,6 +305,31 @@ __global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
     }
 }
 
+// Overflow (reading R14): when a relaxation met a sum the weight type cannot
+// hold, every arc of every reached vertex is tested again with its final
+// distance; a confirmed overflow fails the call with DSSSP_ERR_OVERFLOW.
+template <int DT>
+__global__ void __launch_bounds__(kNaBlock) k_na_verify(NaArgs a) {
+    NaScratch *s = a.s;
+    if (na_vload(&s->ctl.ovf) == 0u || na_vload(&s->ctl.err) != 0) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t u = gw; u < a.n; u += nw) {
+        const uint32_t du = (uint32_t)(__ldcg(&s->packed[u]) >> 32);
+        if (du >= na_inf<DT>()) continue;
+        bool bad = false;
+        for (int64_t k = a.row_ptr[u] + lane; k < a.row_ptr[u + 1]; k += 32) {
+            uint32_t w = a.wbits[k];
+            if (DT == DSSSP_F32 && w == 0x80000000u) w = 0u;
+            bad |= na_add<DT>(du, w) >= na_inf<DT>();
+        }
+        if (__any_sync(0xffffffffu, bad)) {
+            if (lane == 0) atomicCAS(&s->ctl.err, 0, (int)DSSSP_ERR_OVERFLOW);
+            return;
+        }
+    }
+}
+
 template <int DT>
 __global__ void k_na_unpack(NaArgs a) {
     NaScratch *s = a.s;
@@ -347,13 +391,18 @@ extern "C" dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t 
     if (n > (int64_t)kNoAllocMaxVertices) return DSSSP_ERR_TOO_LARGE;
     if (src < 0 || (int64_t)src >= n || !(delta > 0.0) || (dtype != DSSSP_I32 && dtype != DSSSP_F32))
         return DSSSP_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    // the call waits for its result on the host, which a stream being captured
+    // into a CUDA graph does not allow: refuse before any other CUDA call
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) { cudaGetLastError(); return DSSSP_ERR_CUDA; }
+    if (cap != cudaStreamCaptureStatusNone) return DSSSP_ERR_UNSUPPORTED;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return DSSSP_ERR_CUDA; }
     NaScratch *scratch = nullptr;
     int grid = 0;
     dsssp_status st = na_setup(dev, &scratch, &grid);
     if (st != DSSSP_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
     NaArgs a{};
     a.s = scratch;
     a.row_ptr = row_ptr;
@@ -382,6 +431,11 @@ extern "C" dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t 
     if (e == cudaSuccess)
         e = cudaLaunchCooperativeKernel(f32 ? (const void *)k_na_solve<DSSSP_F32> : (const void *)k_na_solve<DSSSP_I32>,
                                         dim3(grid), dim3(kNaBlock), args, 0, s);
+    if (e == cudaSuccess) {
+        if (f32) k_na_verify<DSSSP_F32><<<grid, kNaBlock, 0, s>>>(a);
+        else k_na_verify<DSSSP_I32><<<grid, kNaBlock, 0, s>>>(a);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) {
         if (f32) k_na_unpack<DSSSP_F32><<<(int)(n / kNaBlock + 1), kNaBlock, 0, s>>>(a);
         else k_na_unpack<DSSSP_I32><<<(int)(n / kNaBlock + 1), kNaBlock, 0, s>>>(a);

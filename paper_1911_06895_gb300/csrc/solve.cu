@@ -349,6 +349,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
     const uint32_t T_lo = from_slot ? d.T_lo : 0u;          // only slot entries can be stale
     uint32_t ov_min = inf_key<DT>();
     uint32_t improved = 0, nrec = 0;
+    bool ovf = false;                                       // a sum the weight type cannot hold
     PushCnt q{};
     WarpStage &ws = stage[threadIdx.x >> 5];
     if (from_slot) slot_entries_into_S(a, d, q, ws, gw, nw_all);
@@ -477,6 +478,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
             #pragma unroll
             for (int k = 0; k < kIlp; ++k) {
                 ck[k] = ok[k] ? key_add<DT>(okey[k], arc[k].y) : inf_key<DT>();
+                ovf |= ok[k] && ck[k] >= inf_key<DT>();
                 cur[k] = ck[k] < inf_key<DT>() ? __ldcg(a.packed + arc[k].x) : 0ull;
             }
             // packed[v] only decreases, so a value read earlier bounds it from above:
@@ -509,6 +511,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
             if (LIGHT) atomicAdd(&acc.arcs_light, (unsigned long long)(e1 - e0));
             else atomicAdd(&acc.arcs_heavy, (unsigned long long)(e1 - e0));
         }
+        if (__any_sync(FULL, ovf) && lane == 0) a.ctl->ovf = 1u;
     }
     if (nrec) {
         __syncwarp();
@@ -871,6 +874,28 @@ __device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool 
     return *s_ok != 0;
 }
 
+// Overflow (reading R14: a sum out of a reached vertex that the weight type
+// cannot hold makes the solve fail with DSSSP_ERR_OVERFLOW). A relaxation that
+// met such a sum may have used a distance that decreased later, so when any
+// did, every arc of every reached vertex is tested once more with the final
+// distance, after the last phase. One warp per vertex; runs only in that case.
+template <int DT>
+__device__ void verify_overflow(const SolveArgs &a, uint32_t gw, uint32_t nw) {
+    const uint32_t lane = lane_id();
+    for (uint32_t v = gw; v < a.n; v += nw) {
+        const uint32_t k = (uint32_t)(__ldcg(a.packed + v) >> 32);
+        if (k >= inf_key<DT>()) continue;
+        const uint4 vi = a.vinfo[v];
+        bool bad = false;
+        for (uint32_t e = vi.x + lane; e < vi.z && e < a.m; e += 32u)
+            bad |= key_add<DT>(k, __ldcg(a.arcs + e).y) >= inf_key<DT>();
+        if (__any_sync(FULL, bad)) {
+            if (lane == 0) atomicCAS(&a.ctl->err, 0, (int)DSSSP_ERR_OVERFLOW);
+            return;
+        }
+    }
+}
+
 template <int DT>
 __device__ __forceinline__ void run_phase(const SolveArgs &a, const BlockView &v, BlockAcc &acc, int *slot,
                                           WarpStage *stage, uint32_t gw, uint32_t nw) {
@@ -941,6 +966,7 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(Solv
         }
     }
     __syncthreads();
+    if (vload(&a.ctl->ovf) != 0u && vload(&a.ctl->err) == 0) verify_overflow<DT>(a, gw, nw);
     if (threadIdx.x == 0) flush_stats(a.ctl, acc);
 }
 
@@ -962,6 +988,13 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_phase(SolveArgs a) {
         flush_ov_min(a.ctl, acc, inf_key<DT>());
         flush_stats(a.ctl, acc);
     }
+}
+
+// The overflow check of a stepped solve (see verify_overflow).
+template <int DT>
+__global__ void __launch_bounds__(512) k_verify_overflow(SolveArgs a) {
+    if (vload(&a.ctl->ovf) == 0u || vload(&a.ctl->err) != 0) return;
+    verify_overflow<DT>(a, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, (gridDim.x * blockDim.x) >> 5);
 }
 
 // One warp.
@@ -989,6 +1022,7 @@ __global__ void k_init(SolveArgs a) {
         c->bar_count = 0u;
         c->bar_gen = 0u;
         c->err = 0;
+        c->ovf = 0u;
         c->t_first = 0ull;
         SerialState s{};
         s.mode = MODE_LIGHT;      // B_0 = {s}
@@ -1114,6 +1148,12 @@ cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, in
 cudaError_t launch_serial_step(const SolveArgs &a, cudaStream_t st) {
     if (a.dtype == DSSSP_F32) k_serial<DSSSP_F32><<<1, 32, 0, st>>>(a);
     else k_serial<DSSSP_I32><<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_verify_overflow(const SolveArgs &a, int grid, int block, cudaStream_t st) {
+    if (a.dtype == DSSSP_F32) k_verify_overflow<DSSSP_F32><<<grid, block, 0, st>>>(a);
+    else k_verify_overflow<DSSSP_I32><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 

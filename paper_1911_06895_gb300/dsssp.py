@@ -36,6 +36,7 @@ DSSSP_ERR_OOM = 8
 DSSSP_ERR_UNSUPPORTED = 9
 DSSSP_ERR_TOO_LARGE = 10
 DSSSP_ERR_DEGENERATE = 11
+DSSSP_ERR_OVERFLOW = 12
 
 DSSSP_I32 = 0
 DSSSP_F32 = 1

@@ -103,10 +103,8 @@ def test_edge_cases(ds):
     cases.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (2, 1), (2, 3), (3, 0)],
                                      np.array([0, 0, 0, 0.5, 0], np.float32), dtype=np.float32), 0))
     big = INT_INF - 10
-    cases.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([big, 20, 5], np.int32),
-                                     dtype=np.int32), 0))
-    cases.append((graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([3e38, 3e38], np.float32),
-                                     dtype=np.float32), 0))
+    cases.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([big, 9, 5], np.int32),
+                                     dtype=np.int32), 0))                   # INT32_MAX - 1: the largest distance
     cases.append((graphgen.from_arcs(3, [(0, 1), (0, 2), (1, 2)], np.array([-0.0, 1.0, 0.0], np.float32),
                                      dtype=np.float32), 0))
     # a hub whose arcs span many warps' slices, zero-weight arcs into the source
@@ -128,6 +126,58 @@ def test_edge_cases(ds):
             for opt in MODES:
                 d, p, _ = gpu_solve(ds, h, src, delta, **opt)
                 assert_same(g, src, d, p, d_ref, p_ref, f"case {ci} delta {delta} {opt}")
+        h.close()
+
+
+def overflow_cases():
+    """(graph, source, overflows?) -- reading R14: an overflow is a sum out of a reached
+    vertex, at its final distance, that the weight type cannot hold."""
+    big = INT_INF - 100
+    out = []
+    # a true overflow out of a final distance (int32 and fp32)
+    out.append((graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([INT_INF - 10, 20, 5], np.int32),
+                                   dtype=np.int32), 0, True))
+    out.append((graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([3e38, 3e38], np.float32),
+                                   dtype=np.float32), 0, True))
+    # a sum that overflows only from a distance that later decreases: no overflow.
+    # With one bucket (large Delta) vertex 1 is relaxed first at distance big, then at 2.
+    out.append((graphgen.from_arcs(4, [(0, 1), (0, 2), (2, 1), (1, 3)], np.array([big, 1, 1, 200], np.int32),
+                                   dtype=np.int32), 0, False))
+    out.append((graphgen.from_arcs(4, [(0, 1), (0, 2), (2, 1), (1, 3)], np.array([3e38, 1.0, 1.0, 3e38], np.float32),
+                                   dtype=np.float32), 0, False))
+    # an overflowing arc out of an unreached vertex: ignored
+    out.append((graphgen.from_arcs(3, [(0, 1), (2, 1)], np.array([1, INT_INF - 1], np.int32), dtype=np.int32),
+                0, False))
+    return out
+
+
+def test_overflow_status(ds):
+    for ci, (g, src, overflows) in enumerate(overflow_cases()):
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        if overflows:
+            with pytest.raises(oracle.PathOverflow):
+                oracle.dijkstra(g.row_ptr, g.col, g.w, src)
+        else:
+            d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, src)
+        for delta in (0.5, 4.0, 1e9, math.inf):
+            for opt in MODES:
+                if overflows:
+                    tdt = torch.float32 if g.w.dtype == np.float32 else torch.int32
+                    dist = torch.full((g.n,), 7, dtype=tdt, device="cuda")
+                    pred = torch.full((g.n,), 7, dtype=torch.int32, device="cuda")
+                    with pytest.raises(ds.DsssError) as e:
+                        h.solve(src, delta, dist=dist, pred=pred, options=ds.make_options(**opt) if opt else None)
+                    assert e.value.status == ds.DSSSP_ERR_OVERFLOW, (ci, delta, opt)
+                    assert bool((dist == 7).all()) and bool((pred == 7).all()), "outputs written on overflow"
+                else:
+                    d, p, _ = gpu_solve(ds, h, src, delta, **opt)
+                    assert_same(g, src, d, p, d_ref, p_ref, f"overflow case {ci} delta {delta} {opt}")
+        if overflows:                                   # asynchronous: the status comes from sync()
+            h.solve(src, 1.0, options=ds.make_options(flags=ds.DSSSP_FLAG_ASYNC))
+            with pytest.raises(ds.DsssError) as e:
+                h.sync()
+            assert e.value.status == ds.DSSSP_ERR_OVERFLOW
+            h.sync()
         h.close()
 
 
@@ -283,23 +333,17 @@ def rmat22(ds):
     return g, srcs, deltas, ds.Graph(g.row_ptr, g.col, g.w)
 
 
-def test_full_rmat22_all_deltas_one_source_exact(ds, rmat22):
-    """Full-size scale-22 R-MAT (fp32 U[0,1)), bench launch shape: whole arrays vs Dijkstra."""
+def test_full_rmat22_every_source_every_delta_exact(ds, rmat22):
+    """Full-size scale-22 R-MAT (fp32 U[0,1)), bench launch shape: all 64 sources at all four
+    Deltas, whole arrays element by element against the oracle's Dijkstra."""
     g, srcs, deltas, h = rmat22
-    s = srcs[0]
-    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, s)
-    for delta in deltas:
-        d, p, _ = gpu_solve(ds, h, s, delta)
-        assert_same(g, s, d, p, d_ref, p_ref, f"delta {delta}")
-
-
-def test_full_rmat22_more_sources_invariants(ds, rmat22):
-    """Further sources at full size: the invariant checker (arc inequality, predecessor
-    equality and minimality) on every vertex, plus exact distances at sampled vertices."""
-    g, srcs, deltas, h = rmat22
-    for s, delta in zip(srcs[1:4], deltas):
-        d, p, _ = gpu_solve(ds, h, s, delta)
-        assert oracle.check_invariants(g.row_ptr, g.col, g.w, s, d, p) == 0
+    for c0 in range(0, len(srcs), 16):
+        chunk = srcs[c0:c0 + 16]
+        refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, chunk)
+        for s, d_ref, p_ref in zip(chunk, refd, refp):
+            for delta in deltas:
+                d, p, _ = gpu_solve(ds, h, s, delta)
+                assert_same(g, s, d, p, d_ref, p_ref, f"source {s} delta {delta}")
 
 
 def test_full_grid4096_all_deltas_exact(ds):

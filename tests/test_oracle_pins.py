@@ -187,21 +187,47 @@ def test_star_and_unreachable():
         assert list(p[1:9]) == [0] * 8
 
 
-def test_int32_saturation_reads_unreachable():
+def test_int32_overflow_is_an_error():
+    """Reading R14: a sum >= INT32_MAX out of a reached vertex is an overflow, reported
+    by every solver; one below it is an ordinary distance."""
     big = INT_INF - 10
     g = graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([big, 20, 5], np.int32), dtype=np.int32)
     for name in ALL_SOLVERS:
+        with pytest.raises(oracle.PathOverflow):
+            solve(name, g, 0, delta=100.0)
+    g = graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([big, 9, 5], np.int32), dtype=np.int32)
+    for name in ALL_SOLVERS:
         d, p = solve(name, g, 0, delta=100.0)
         assert d[1] == big and p[1] == 0
-        assert d[2] == INT_INF and p[2] == -1     # big + 20 saturates
+        assert d[2] == INT_INF - 1 and p[2] == 1            # the largest distance that fits
         assert d[3] == 5
 
 
-def test_fp32_overflow_reads_unreachable():
+def test_fp32_overflow_is_an_error():
     g = graphgen.from_arcs(3, [(0, 1), (1, 2)], np.array([3e38, 3e38], np.float32), dtype=np.float32)
     for name in ALL_SOLVERS:
-        d, p = solve(name, g, 0, delta=1e38)     # the LA form steps through every bucket index
-        assert d[1] == np.float32(3e38) and np.isinf(d[2]) and p[2] == -1
+        with pytest.raises(oracle.PathOverflow):
+            solve(name, g, 0, delta=1e38)     # the LA form steps through every bucket index
+
+
+def test_overflow_only_counts_final_distances():
+    """The overflow condition uses final distances: a long detour whose sum would not
+    fit is irrelevant when a shorter path gives the vertex a small distance."""
+    big = INT_INF - 100
+    arcs = [(0, 1), (1, 2), (0, 2), (2, 3)]
+    w = np.array([big, 50, 1, 200], np.int32)     # 0->1->2 gives big+50; 0->2 gives 1
+    g = graphgen.from_arcs(4, arcs, w, dtype=np.int32)
+    for name in ALL_SOLVERS:
+        d, p = solve(name, g, 0, delta=100.0)
+        assert list(d) == [0, big, 1, 201] and list(p) == [0, 0, 0, 2]
+
+
+def test_overflow_out_of_an_unreached_vertex_is_ignored():
+    big = INT_INF - 1
+    g = graphgen.from_arcs(3, [(0, 1), (2, 1)], np.array([1, big], np.int32), dtype=np.int32)
+    for name in ALL_SOLVERS:
+        d, p = solve(name, g, 0, delta=10.0)
+        assert list(d) == [0, 1, INT_INF] and list(p) == [0, 0, -1]
 
 
 def test_zero_weight_from_source_and_zero_cycle():
@@ -348,6 +374,55 @@ def test_invariant_checker_catches_planted_mistakes():
     assert oracle.check_invariants(g.row_ptr, g.col, g.w, s, d, p_bad) > 0
     p_bad = p.copy(); p_bad[s] = -1
     assert oracle.check_invariants(g.row_ptr, g.col, g.w, s, d, p_bad) > 0
+
+
+def test_invariant_checker_catches_cyclic_labelling():
+    """A labelling too small on a cycle of zero-effect arcs passes the arc inequality and
+    the predecessor rules; realisability and the predecessor chains catch it."""
+    # 0 -> 1 (5); 1 <-> 2 with zero weights; 2 -> 3 (1). Truth: d = [0, 5, 5, 6].
+    arcs = [(0, 1), (1, 2), (2, 1), (2, 3)]
+    for dtype, w in ((np.int32, [5, 0, 0, 1]), (np.float32, [5.0, 0.0, 0.0, 1.0])):
+        g = graphgen.from_arcs(4, arcs, np.array(w, dtype), dtype=dtype)
+        d, p = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
+        assert oracle.check_invariants(g.row_ptr, g.col, g.w, 0, d, p) == 0
+        bogus_d = np.array([0, 2, 2, 3], dtype)                      # 1 and 2 too small
+        bogus_p = np.array([0, 2, 1, 2], np.int32)                   # each the other's pred
+        assert oracle.check_invariants(g.row_ptr, g.col, g.w, 0, bogus_d, bogus_p) >= 3
+    # the same trap with positive weights absorbed by float32 rounding (spacing 2 at 2^24)
+    big = float(2 ** 24)
+    g = graphgen.from_arcs(4, arcs, np.array([big + 8, 0.5, 0.5, 1.0], np.float32), dtype=np.float32)
+    d, p = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
+    assert oracle.check_invariants(g.row_ptr, g.col, g.w, 0, d, p) == 0
+    bogus_d = np.array([0, big, big, big], np.float32)
+    bogus_p = np.array([0, 2, 1, 2], np.int32)
+    assert oracle.check_invariants(g.row_ptr, g.col, g.w, 0, bogus_d, bogus_p) >= 3
+
+
+def test_invariant_checker_accepts_a_legal_zero_weight_pred_cycle():
+    """With zero weights the smallest-id rule can close a predecessor cycle on correct
+    distances (source 2; 0 and 1 both at distance 1 and each other's smallest tight
+    in-neighbour). Realisability holds, so the checker accepts it."""
+    arcs = [(2, 0), (2, 1), (0, 1), (1, 0)]
+    g = graphgen.from_arcs(3, arcs, np.array([1, 1, 0, 0], np.int32), dtype=np.int32)
+    d, p = oracle.dijkstra(g.row_ptr, g.col, g.w, 2)
+    assert list(d) == [1, 1, 0] and list(p) == [1, 0, 2]
+    assert oracle.check_invariants(g.row_ptr, g.col, g.w, 2, d, p) == 0
+    p_bad = p.copy(); p_bad[0] = 2                               # not the smallest tight in-neighbour
+    assert oracle.check_invariants(g.row_ptr, g.col, g.w, 2, d, p_bad) > 0
+
+
+def test_invariant_checker_catches_a_broken_chain_on_random_graphs():
+    """Planted on large random labellings: a reached vertex whose only tight walk is
+    removed by raising the source's outgoing distances is flagged (realisability)."""
+    g = graphgen.rmat(10, 16, seed=23)
+    g.w = graphgen.weights_unit(g.m, 23)
+    s = int(graphgen.random_sources(g, 1, 23)[0])
+    d, p = oracle.dijkstra(g.row_ptr, g.col, g.w, s)
+    assert oracle.check_invariants(g.row_ptr, g.col, g.w, s, d, p) == 0
+    reached = np.flatnonzero(np.isfinite(d) & (np.arange(g.n) != s))
+    v = int(reached[0])
+    d_bad = d.copy(); d_bad[v] = np.float32(0.0)                  # v claims distance 0
+    assert oracle.check_invariants(g.row_ptr, g.col, g.w, s, d_bad, p) > 0
 
 
 def test_all_forms_agree_many_deltas_fp32():
