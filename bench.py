@@ -56,7 +56,7 @@ B_VERTEX, B_ARC, B_FAR, B_INIT_UNPACK = 28, 16, 20, 36
 
 
 # DRAM traffic of k_solve_persistent per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum), mean of
-# one launch at each Delta of the sweep (profiles/k_solve_persistent_rmat22_traffic_by_delta.md). It holds only
+# one launch at each Delta of the sweep, from one ncu capture of the profiling driver below. It holds only
 # for the kernel source the counters were taken on; any other source reports null.
 TRAFFIC_BYTES_PER_LAUNCH = 3.104e9
 TRAFFIC_SOURCE_SHA256 = "b614af92c02160f64bd3e03b7982156960ee42754320469267359524b348a07b"
@@ -249,9 +249,17 @@ def main():
         profile_backward_driver(args)
         return
 
+    if "WORLD_SIZE" not in os.environ and args.gpus > 1:
+        # --gpus N without a launcher: start N ranks on this node (one process per GPU)
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", os.environ.get("MASTER_PORT", "29517"),
+               os.path.abspath(__file__), *sys.argv[1:]]
+        sys.exit(subprocess.call(cmd))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        sys.exit(f"bench.py: --gpus {args.gpus} but the launcher started {world} ranks")
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
@@ -562,8 +570,63 @@ def run_extras(ds, torch):
         "plain_solve_ms": ms_p, "plain_solve_gteps": sm / (ms_p * 1e-3) / 1e9,
         "fwd_bwd_over_fwd": ms_fb / ms_f, "tune_s": tune_s}
 
-    # (d) ablation: the paper's dense-vector form (t_Bi and S as per-vertex stamps scanned
-    # in full every phase, dsssp_solve_noalloc) against the list-based solve, scale-17 R-MAT
+    out.update(run_ablation(ds, torch))
+    out["other_workloads"] = run_other_workloads(ds, torch)
+    return out
+
+
+def _timed_solves(torch, calls, sync_each: bool) -> float:
+    """CUDA-event ms over a list of calls (one warm-up pass first); with sync_each the
+    host waits after every call, as a synchronous entry point does."""
+    for c in calls[:1]:
+        c()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t = time.perf_counter()
+    a.record()
+    for c in calls:
+        c()
+        if sync_each:
+            torch.cuda.synchronize()
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) if not sync_each else (time.perf_counter() - t) * 1e3
+
+
+def run_ablation(ds, torch):
+    """The paper's full-vector form (t_Bi, S and the far pile as per-vertex stamps scanned in
+    full every phase, row filters fused into the scans) against the list-based persistent
+    solve: (1) DSSSP_MODE_DENSE on the bench graph itself (scale-22 R-MAT, 4 sources per
+    Delta, both arms asynchronous, CUDA events around all solves of a Delta); (2)
+    dsssp_solve_noalloc (the same form in a fixed array, n <= 131,072) on a scale-17 R-MAT,
+    where each call waits for its result: both arms then wait after every solve and are
+    timed on the host."""
+    import graphgen.workloads as W
+    out = {}
+    g, srcs, deltas = W.rmat22_unit(n_sources=4)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
+    pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
+    o_list = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
+    o_dense = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=ds.DSSSP_MODE_DENSE)
+    per = {}
+    for d in deltas:
+        h.prepare(d)
+        ms_l = _timed_solves(torch, [lambda s=s: h.solve(s, d, dist=dist, pred=pred, options=o_list) for s in srcs],
+                             False) / len(srcs)
+        ms_d = _timed_solves(torch, [lambda s=s: h.solve(s, d, dist=dist, pred=pred, options=o_dense) for s in srcs],
+                             False) / len(srcs)
+        h.sync()
+        st = h.solve(srcs[0], d, dist=dist, pred=pred, options=ds.make_options(mode=ds.DSSSP_MODE_DENSE),
+                     stats=True).stats
+        per[str(d)] = {"dense_ms_per_solve": ms_d, "list_ms_per_solve": ms_l, "list_speedup": ms_d / ms_l,
+                       "dense_gteps": g.m / (ms_d * 1e-3) / 1e9, "list_gteps": g.m / (ms_l * 1e-3) / 1e9,
+                       "dense_phases": st["light_phases"] + st["heavy_phases"]}
+    h.close()
+    out["ablation_dense_vs_lists"] = {
+        "workload": f"rmat22_unit n={g.n} m={g.m}, {len(srcs)} sources per Delta (the bench graph)",
+        "timing": "both arms asynchronous; CUDA events around the solves of one Delta", "per_delta": per}
+
     g, srcs, _ = W.rmat22_unit(scale=17, n_sources=8)
     rp = torch.from_numpy(g.row_ptr).cuda()
     cl = torch.from_numpy(g.col).cuda()
@@ -572,25 +635,56 @@ def run_extras(ds, torch):
     dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
     pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
+    o_sync = ds.make_options()
     abl = {}
     for d in (0.05, 0.1, 0.5):
         h.prepare(d)
-
-        def dense():
-            for s in srcs:
-                ds.check(ds.dsssp_solve_noalloc(g.n, g.m, rp.data_ptr(), cl.data_ptr(), ww.data_ptr(), ds.DSSSP_F32,
-                                                s, d, dist.data_ptr(), pred.data_ptr(),
-                                                ds._stream_ptr(stream)), "dsssp_solve_noalloc")
-
-        def lists():
-            for s in srcs:
-                h.solve(s, d, dist=dist, pred=pred, options=o_async)
-        ms_d = _events_ms(torch, dense, 1) / len(srcs)
-        ms_l = _events_ms(torch, lists, 1) / len(srcs)
-        h.sync()
-        abl[str(d)] = {"dense_ms_per_solve": ms_d, "list_ms_per_solve": ms_l, "list_speedup": ms_d / ms_l}
+        na = [lambda s=s: ds.check(ds.dsssp_solve_noalloc(g.n, g.m, rp.data_ptr(), cl.data_ptr(), ww.data_ptr(),
+                                                          ds.DSSSP_F32, s, d, dist.data_ptr(), pred.data_ptr(),
+                                                          ds._stream_ptr(stream)), "dsssp_solve_noalloc")
+              for s in srcs]
+        ls = [lambda s=s: h.solve(s, d, dist=dist, pred=pred, options=o_sync) for s in srcs]
+        ms_d = _timed_solves(torch, na, True) / len(srcs)
+        ms_l = _timed_solves(torch, ls, True) / len(srcs)
+        abl[str(d)] = {"noalloc_ms_per_solve": ms_d, "list_ms_per_solve": ms_l, "list_speedup": ms_d / ms_l}
     h.close()
-    out["ablation_dense_vs_lists"] = {"workload": f"rmat17_unit n={g.n} m={g.m}, 8 sources", "per_delta": abl}
+    out["ablation_noalloc_vs_lists"] = {
+        "workload": f"rmat17_unit n={g.n} m={g.m}, 8 sources",
+        "timing": "both arms wait for every solve (the no-allocation call is synchronous); host wall time",
+        "per_delta": abl}
+    return out
+
+
+def run_other_workloads(ds, torch):
+    """The other single-source workloads: the 4096 x 4096 grid (int32 U{1..1000}, 5 % of arcs
+    dropped, corner source, Delta in {100, 1000, 10000}: the high-diameter, phase-bound case)
+    and the scale-14 R-MAT (int32 U{1..255}, Delta 32, highest out-degree source). Per Delta:
+    device time per solve (CUDA events, median of several), GTEPS, phases and the algorithmic
+    bandwidth of the solve against the measured HBM copy peak."""
+    import graphgen.workloads as W
+    peak, _ = measured_peak_gbs()
+    out = {}
+    for name, (g, srcs, deltas), reps in (("grid4096_int", W.grid4096(), 3), ("rmat14_int", W.rmat14_int(), 20)):
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        tdt = torch.int32
+        dist = torch.empty(g.n, dtype=tdt, device="cuda")
+        pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        s = srcs[0]
+        per = {}
+        for d in deltas:
+            h.prepare(d)
+            st = h.solve(s, d, dist=dist, pred=pred, stats=True).stats
+            o = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
+            ms = _events_ms(torch, lambda: h.solve(s, d, dist=dist, pred=pred, options=o), reps)
+            h.sync()
+            b = algorithmic_bytes(st, g.n)
+            per[str(d)] = {"ms_per_solve": ms, "gteps": g.m / (ms * 1e-3) / 1e9,
+                           "phases": st["light_phases"] + st["heavy_phases"] + st["rebin_phases"],
+                           "buckets": st["buckets"], "arcs_relaxed": st["arcs_light"] + st["arcs_heavy"],
+                           "roofline": {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": peak,
+                                        "unit": "GB/s", "frac": b / (ms * 1e-3) / 1e9 / peak}}
+        h.close()
+        out[name] = {"n": g.n, "m": g.m, "source": s, "per_delta": per}
     return out
 
 

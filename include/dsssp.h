@@ -74,7 +74,13 @@ typedef struct dsssp_graph dsssp_graph;
 /* Solver execution schemes (dsssp_options.mode). */
 typedef enum {
     DSSSP_MODE_PERSISTENT = 0,   /* one cooperative kernel runs every phase; grid-wide barriers  */
-    DSSSP_MODE_STEPPED = 1       /* one kernel launch per phase, loop driven by the host          */
+    DSSSP_MODE_STEPPED = 1,      /* one kernel launch per phase, loop driven by the host          */
+    DSSSP_MODE_DENSE = 2         /* the paper's full-vector form (Fig. 1 left; the filter fusion of
+                                    Section VI-B): t_Bi, S and the far pile are per-vertex stamps,
+                                    every phase scans all n of them and filters each scanned row
+                                    into light or heavy arcs on the fly. Same results; block_size,
+                                    grid_size, solo_work, flags other than ASYNC and test_hook are
+                                    ignored; stats fill buckets, light_phases and heavy_phases. */
 } dsssp_mode;
 
 /* dsssp_options.flags */

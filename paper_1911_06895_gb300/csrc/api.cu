@@ -5,6 +5,7 @@
 #include <cstring>
 #include <new>
 
+#include "dense.cuh"
 #include "graph.cuh"
 
 using namespace dsssp;
@@ -73,8 +74,8 @@ dsssp_status ensure_split(dsssp_graph *g, double delta, cudaStream_t st, Split *
 
 namespace {
 
-__global__ void k_sticky(const Ctl *c, int32_t *sticky) {
-    int e = *(const volatile int *)&c->err;
+__global__ void k_sticky(const int32_t *err, int32_t *sticky) {
+    int e = *(const volatile int *)err;
     if (e != 0) atomicCAS(sticky, 0, e);
 }
 
@@ -97,6 +98,7 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     const size_t o_ov0 = bytes;    bytes += up(n * 4);
     const size_t o_ov1 = bytes;    bytes += up(n * 4);
     const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
+    const size_t o_nactl = bytes;  bytes += up(sizeof(NaCtl));
     const size_t o_sticky = bytes; bytes += up(sizeof(int32_t));
     char *base = nullptr;
     DSSSP_TRY(cudaMalloc(&base, bytes));
@@ -120,6 +122,7 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     a.OV1 = (uint32_t *)(base + o_ov1);
     a.ctl = (Ctl *)(base + o_ctl);
     g->ctl = a.ctl;
+    g->nactl = (NaCtl *)(base + o_nactl);
     g->sticky = (int32_t *)(base + o_sticky);
     return DSSSP_OK;
 }
@@ -286,9 +289,40 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     }
     if (opt.block_size < 32 || opt.block_size > 512 || opt.block_size % 32 != 0) return DSSSP_ERR_INVALID_ARG;
     if (opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
-    if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED) return DSSSP_ERR_INVALID_ARG;
+    if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED && opt.mode != DSSSP_MODE_DENSE)
+        return DSSSP_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (opt.mode == DSSSP_MODE_DENSE) {
+        // the full-vector form on the handle's own CSR; working memory from the workspace
+        dsssp_status rc = ensure_workspace(g);
+        if (rc != DSSSP_OK) return rc;
+        NaMem mem;
+        mem.packed = g->args.packed;
+        mem.fstamp = g->args.near_stamp;
+        mem.sstamp = g->args.s_stamp;
+        mem.far = g->args.b_stamp;
+        mem.ctl = g->nactl;
+        DSSSP_TRY(dense_solve_launch(g->off, g->col, g->wbits, g->dtype, (uint32_t)g->n, (uint32_t)g->m,
+                                     (uint32_t)src, delta, mem, dist, pred, opt.timeout_ns, opt.max_phases, st));
+        k_sticky<<<1, 1, 0, st>>>(&g->nactl->err, g->sticky);
+        DSSSP_TRY(cudaGetLastError());
+        if ((opt.flags & DSSSP_FLAG_ASYNC) && !stats) return DSSSP_OK;
+        NaCtl hc;
+        DSSSP_TRY(cudaMemcpyAsync(&hc, g->nactl, sizeof(NaCtl), cudaMemcpyDeviceToHost, st));
+        DSSSP_TRY(cudaStreamSynchronize(st));
+        if (stats) {
+            std::memset(stats, 0, sizeof *stats);
+            stats->buckets = hc.buckets + 1;
+            stats->light_phases = hc.n_light;
+            stats->heavy_phases = hc.n_heavy;
+        }
+        if (hc.err != 0) {
+            cudaMemsetAsync(g->sticky, 0, sizeof(int32_t), st);
+            return (dsssp_status)hc.err;
+        }
+        return DSSSP_OK;
+    }
     Split *sp = nullptr;
     dsssp_status rc = ensure_split(g, delta, st, &sp);
     if (rc != DSSSP_OK) return rc;
@@ -340,7 +374,7 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
         DSSSP_TRY(launch_verify_overflow(a, grid, opt.block_size, st));
     }
     DSSSP_TRY(launch_unpack(a, dist, pred, st));
-    k_sticky<<<1, 1, 0, st>>>(g->ctl, g->sticky);
+    k_sticky<<<1, 1, 0, st>>>(&g->ctl->err, g->sticky);
     DSSSP_TRY(cudaGetLastError());
     if ((opt.flags & DSSSP_FLAG_ASYNC) && !stats) return DSSSP_OK;
     DSSSP_TRY(cudaMemcpyAsync(g->ctl_host, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));

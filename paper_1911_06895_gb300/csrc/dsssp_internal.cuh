@@ -141,8 +141,8 @@ struct alignas(64) PhaseDesc {
     uint32_t count2;        // first round: heavy-only entries of the slot
     uint32_t ov_cur;        // overflow list read by REBIN / appended to otherwise
     uint32_t solo;          // 1: block 0 alone runs this phase (little work), the others wait
-    uint32_t wbase32;       // first bucket of the slot window (low 32 bits, for slot stamps)
     uint32_t pad;
+    uint32_t wepoch;        // window epoch: changes whenever the window's thresholds do
     uint32_t count_h;       // FUSED: entries of the S list whose heavy arcs are relaxed
     uint32_t arcs_h;        // FUSED: their heavy arcs
 };
@@ -156,19 +156,27 @@ struct alignas(16) SerialState {
     int64_t phases;
     uint64_t t_last;        // %globaltimer at the previous barrier
     uint64_t t_start;
-    uint64_t pad0;
+    uint32_t wepoch;        // window epoch (refills of the slot window)
+    uint32_t pad0;
     long long st[16];
 };
+
+// The published view of the next phase: kViewWords 64-bit words, each the
+// phase number (high half) and one 32-bit field (low half). A word is written
+// and read as one 8-byte access, so a reader that sees the same phase number
+// in every word holds a consistent view without a separate flag or fence.
+constexpr int kViewWords = 13;
 
 struct Ctl {
     // barrier words, alone on their line
     unsigned int bar_count;
-    unsigned int bar_gen;
+    unsigned int pad_b;
     int32_t err;            // first dsssp_status != OK
     uint32_t ovf;           // 1: a relaxation met a sum the weight type cannot hold (checked at the end)
     uint64_t t_first;       // %globaltimer of the first arrival at the current barrier
     uint32_t pad1[26];
-    PhaseDesc desc;
+    unsigned long long view[16];   // the published view (kViewWords used), on its own line
+    PhaseDesc desc;                // the serial step's own copy of the current phase
     // key thresholds of the window: bucket wbase + t starts at key thr[t]
     uint32_t thr[kSlots + 1];
     uint32_t pad2[15];

@@ -3,6 +3,7 @@
 // Not part of the public ABI.
 #pragma once
 
+#include "dense.cuh"
 #include "dsssp_internal.cuh"
 
 namespace dsssp {
@@ -65,6 +66,7 @@ struct dsssp_graph {
     size_t ws_bytes = 0;
     dsssp::SolveArgs args{};
     dsssp::Ctl *ctl = nullptr;           // device
+    dsssp::NaCtl *nactl = nullptr;       // device: control words of DSSSP_MODE_DENSE solves
     dsssp::Ctl *ctl_host = nullptr;      // pinned host mirror
     int32_t *sticky = nullptr;    // device: first error of asynchronous solves
     int occ_block = 0, occ_blocks_per_sm = 0;

@@ -15,9 +15,16 @@
 // Every call uses the same array: calls that overlap on the GPU (for example
 // on two streams) race and must be serialised by the caller. Each call clears
 // the state it needs before using it.
+//
+// The same kernels, on working memory allocated with a graph handle, are the
+// DSSSP_MODE_DENSE scheme of dsssp_solve: the paper's full-vector form (every
+// phase scans all n entries of t_Bi, S or the far pile; the A_L / A_H filters
+// fused into the row scans, Section VI-B) as an alternative to the compacted
+// lists of the persistent solver.
 #include <mutex>
 
 #include "dsssp_internal.cuh"
+#include "dense.cuh"
 
 namespace {
 
@@ -25,24 +32,6 @@ using namespace dsssp;
 
 constexpr uint32_t kNoAllocMaxVertices = 1u << 17;   // 131,072
 constexpr int kNaBlock = 256;
-
-// Per-call control words.
-struct NaCtl {
-    unsigned int bar_count;
-    unsigned int bar_gen;
-    int32_t err;              // first dsssp_status != OK
-    int32_t flags;            // input validation: bit 0 malformed CSR, bit 1 bad weight
-    uint32_t mode;            // 0 light round, 1 heavy pass, 2 next-bucket search, 3 done
-    uint32_t round;           // frontier stamp of the current light round
-    uint32_t epoch;           // S stamp of the current bucket
-    uint32_t T;               // key < T  <=>  bucket <= i
-    uint32_t next_count;      // vertices stamped for the next light round
-    uint32_t far_min;         // lower bound on the keys of far (later-bucket) vertices
-    uint32_t far_count;       // vertices on the far pile
-    uint32_t ovf;             // 1: a relaxation met a sum the weight type cannot hold
-    long long phases;
-    unsigned long long progress;   // bumped as rows are scanned: a waiting block's clock restarts on it
-};
 
 struct NaScratch {
     unsigned long long packed[kNoAllocMaxVertices];   // key << 32 | pred
@@ -119,9 +108,10 @@ __device__ bool na_barrier(NaCtl *c, uint32_t nblocks, int64_t timeout_ns, F ser
     return ok != 0;
 }
 
+template <typename RP>
 struct NaArgs {
-    NaScratch *s;                 // device address of g_noalloc_scratch
-    const int64_t *row_ptr;
+    NaMem s;                      // working memory (the fixed array, or a graph handle's)
+    const RP *row_ptr;            // int64 (caller's CSR) or uint32 (a graph handle's copy)
     const int32_t *col;
     const uint32_t *wbits;
     void *dist;
@@ -131,32 +121,35 @@ struct NaArgs {
     int64_t max_phases;
     uint32_t n, m, src, light_max;
     uint32_t nblocks;
+    uint32_t validate;            // 1: check the CSR and the weights first
 };
 
 // Clear the state of the previous call, check the CSR, seed t[s] = 0.
-template <int DT>
-__global__ void k_na_init(NaArgs a) {
-    NaScratch *s = a.s;
+template <int DT, typename RP>
+__global__ void k_na_init(NaArgs<RP> a) {
+    const NaMem &s = a.s;
     const uint32_t stride = gridDim.x * blockDim.x;
     const unsigned long long unreached = ((unsigned long long)na_inf<DT>() << 32) | NO_PRED;
     int bad = 0;
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += stride) {
-        s->packed[v] = v == a.src ? (unsigned long long)a.src : unreached;
-        s->fstamp[v] = v == a.src ? 1u : 0u;
-        s->sstamp[v] = 0u;
-        s->far[v] = 0u;
-        const int64_t b = a.row_ptr[v], e = a.row_ptr[v + 1];
-        if (b < 0 || e < b || e > (int64_t)a.m) bad |= 1;
+        s.packed[v] = v == a.src ? (unsigned long long)a.src : unreached;
+        s.fstamp[v] = v == a.src ? 1u : 0u;
+        s.sstamp[v] = 0u;
+        s.far[v] = 0u;
+        if (a.validate) {
+            const int64_t b = (int64_t)a.row_ptr[v], e = (int64_t)a.row_ptr[v + 1];
+            if (b < 0 || e < b || e > (int64_t)a.m) bad |= 1;
+        }
     }
-    for (int64_t e = blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)a.m; e += stride) {
+    for (int64_t e = blockIdx.x * blockDim.x + threadIdx.x; a.validate && e < (int64_t)a.m; e += stride) {
         const int32_t h = a.col[e];
         if (h < 0 || (uint32_t)h >= a.n) bad |= 1;
         const uint32_t w = a.wbits[e];
         if (DT == DSSSP_F32 ? (w >= 0x7F800000u && w != 0x80000000u) : (int32_t)w < 0) bad |= 2;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        if (a.row_ptr[0] != 0 || a.row_ptr[a.n] != (int64_t)a.m) bad |= 1;
-        NaCtl &c = s->ctl;
+        if (a.validate && (a.row_ptr[0] != 0 || (int64_t)a.row_ptr[a.n] != (int64_t)a.m)) bad |= 1;
+        NaCtl &c = *s.ctl;
         c.bar_count = 0u;
         c.bar_gen = 0u;
         c.err = 0;
@@ -169,20 +162,20 @@ __global__ void k_na_init(NaArgs a) {
         c.far_count = 0u;
         c.phases = 0;
     }
-    if (bad) atomicOr(&s->ctl.flags, bad);
+    if (bad) atomicOr(&s.ctl->flags, bad);
 }
 
 // Relax arcs [b, e) of row u (light ones or heavy ones) from key du, one warp.
-template <int DT>
-__device__ void na_relax_row(const NaArgs &a, uint32_t u, uint32_t du, bool light, uint32_t T, uint32_t round,
+template <int DT, typename RP>
+__device__ void na_relax_row(const NaArgs<RP> &a, uint32_t u, uint32_t du, bool light, uint32_t T, uint32_t round,
                              uint32_t &far_min, uint32_t &next, uint32_t &farn) {
-    NaScratch *s = a.s;
+    const NaMem &s = a.s;
     const uint32_t lane = threadIdx.x & 31u;
-    const int64_t b = a.row_ptr[u], e = a.row_ptr[u + 1];
+    const int64_t b = (int64_t)a.row_ptr[u], e = (int64_t)a.row_ptr[u + 1];
     bool ovf = false;
     for (int64_t k = b + lane; k < e; k += 32) {
         // a long row tells waiting blocks that it advances (every 64 x 32 arcs)
-        if (lane == 0 && ((k - b) & 2047) == 2047 - 31) atomicAdd(&s->ctl.progress, 1ull);
+        if (lane == 0 && ((k - b) & 2047) == 2047 - 31) atomicAdd(&s.ctl->progress, 1ull);
         uint32_t w = a.wbits[k];
         if (DT == DSSSP_F32 && w == 0x80000000u) w = 0u;            // -0.0 is +0.0
         if ((w <= a.light_max) != light) continue;                   // A_L o t_Bi  /  A_H o S
@@ -190,23 +183,23 @@ __device__ void na_relax_row(const NaArgs &a, uint32_t u, uint32_t du, bool ligh
         const uint32_t ck = na_add<DT>(du, w);
         if (ck >= na_inf<DT>()) { ovf = true; continue; }           // checked again at the end
         const unsigned long long cand = ((unsigned long long)ck << 32) | u;
-        if (cand >= __ldcg(&s->packed[v])) continue;
-        const unsigned long long old = atomicMin(&s->packed[v], cand);
+        if (cand >= __ldcg(&s.packed[v])) continue;
+        const unsigned long long old = atomicMin(&s.packed[v], cand);
         if (cand >= old || (uint32_t)(old >> 32) <= ck) continue;      // no strict decrease
         if (ck < T) {                                               // back into bucket i
-            if (atomicExch(&s->fstamp[v], round + 1u) != round + 1u) ++next;
+            if (atomicExch(&s.fstamp[v], round + 1u) != round + 1u) ++next;
         } else {                                                    // a later bucket
             far_min = min(far_min, ck);
-            if (atomicExch(&s->far[v], 1u) == 0u) ++farn;
+            if (atomicExch(&s.far[v], 1u) == 0u) ++farn;
         }
     }
-    if (__any_sync(0xffffffffu, ovf) && lane == 0) s->ctl.ovf = 1u;
+    if (__any_sync(0xffffffffu, ovf) && lane == 0) s.ctl->ovf = 1u;
 }
 
-template <int DT>
-__global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
-    NaScratch *s = a.s;
-    NaCtl *c = &s->ctl;
+template <int DT, typename RP>
+__global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs<RP> a) {
+    const NaMem &s = a.s;
+    NaCtl *c = s.ctl;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -233,16 +226,16 @@ __global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
             const uint32_t v = base + lane;
             bool sel = false;
             if (v < a.n) {
-                if (mode == 0u) sel = __ldcg(&s->fstamp[v]) == round;          // t_Bi
-                else if (mode == 1u) sel = __ldcg(&s->sstamp[v]) == epoch;     // S
-                else sel = __ldcg(&s->far[v]) == 1u;                            // far pile
+                if (mode == 0u) sel = __ldcg(&s.fstamp[v]) == round;          // t_Bi
+                else if (mode == 1u) sel = __ldcg(&s.sstamp[v]) == epoch;     // S
+                else sel = __ldcg(&s.far[v]) == 1u;                            // far pile
             }
             if (mode == 2u) {                                                  // next-bucket search
                 if (sel) {
-                    const uint32_t k = (uint32_t)(__ldcg(&s->packed[v]) >> 32);
+                    const uint32_t k = (uint32_t)(__ldcg(&s.packed[v]) >> 32);
                     if (k < T) {
-                        s->far[v] = 0u;
-                        if (atomicExch(&s->fstamp[v], round + 1u) != round + 1u) ++next;
+                        s.far[v] = 0u;
+                        if (atomicExch(&s.fstamp[v], round + 1u) != round + 1u) ++next;
                     } else {
                         far_min = min(far_min, k);
                         ++farn;
@@ -255,12 +248,12 @@ __global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
                 const int l = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const uint32_t u = base + (uint32_t)l;
-                const uint32_t du = (uint32_t)(__ldcg(&s->packed[u]) >> 32);
+                const uint32_t du = (uint32_t)(__ldcg(&s.packed[u]) >> 32);
                 if (mode == 0u && lane == 0) {       // S = S u t_Bi; a far key of u is now stale
-                    s->sstamp[u] = epoch;
-                    s->far[u] = 0u;
+                    s.sstamp[u] = epoch;
+                    s.far[u] = 0u;
                 }
-                na_relax_row<DT>(a, u, du, mode == 0u, T, round, far_min, next, farn);
+                na_relax_row<DT, RP>(a, u, du, mode == 0u, T, round, far_min, next, farn);
             }
         }
         if (far_min < na_inf<DT>()) atomicMin(&b_far_min, far_min);
@@ -284,6 +277,9 @@ __global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
             }
             const uint32_t next_count = c->next_count;
             c->next_count = 0u;
+            if (mode == 0u) c->n_light += 1;
+            else if (mode == 1u) c->n_heavy += 1;
+            else c->n_select += 1;
             if (mode == 1u) c->epoch += 1u;
             if (next_count) {                                    // while t_Bi != 0: another light round
                 c->round += 1u;
@@ -299,6 +295,7 @@ __global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
             c->T = T;
             c->far_min = na_inf<DT>();
             c->far_count = 0u;
+            c->buckets += 1;
             c->mode = 2u;
         });
         if (!ok) break;
@@ -308,34 +305,34 @@ __global__ void __launch_bounds__(kNaBlock) k_na_solve(NaArgs a) {
 // Overflow (reading R14): when a relaxation met a sum the weight type cannot
 // hold, every arc of every reached vertex is tested again with its final
 // distance; a confirmed overflow fails the call with DSSSP_ERR_OVERFLOW.
-template <int DT>
-__global__ void __launch_bounds__(kNaBlock) k_na_verify(NaArgs a) {
-    NaScratch *s = a.s;
-    if (na_vload(&s->ctl.ovf) == 0u || na_vload(&s->ctl.err) != 0) return;
+template <int DT, typename RP>
+__global__ void __launch_bounds__(kNaBlock) k_na_verify(NaArgs<RP> a) {
+    const NaMem &s = a.s;
+    if (na_vload(&s.ctl->ovf) == 0u || na_vload(&s.ctl->err) != 0) return;
     const uint32_t lane = threadIdx.x & 31u;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t u = gw; u < a.n; u += nw) {
-        const uint32_t du = (uint32_t)(__ldcg(&s->packed[u]) >> 32);
+        const uint32_t du = (uint32_t)(__ldcg(&s.packed[u]) >> 32);
         if (du >= na_inf<DT>()) continue;
         bool bad = false;
-        for (int64_t k = a.row_ptr[u] + lane; k < a.row_ptr[u + 1]; k += 32) {
+        for (int64_t k = (int64_t)a.row_ptr[u] + lane; k < (int64_t)a.row_ptr[u + 1]; k += 32) {
             uint32_t w = a.wbits[k];
             if (DT == DSSSP_F32 && w == 0x80000000u) w = 0u;
             bad |= na_add<DT>(du, w) >= na_inf<DT>();
         }
         if (__any_sync(0xffffffffu, bad)) {
-            if (lane == 0) atomicCAS(&s->ctl.err, 0, (int)DSSSP_ERR_OVERFLOW);
+            if (lane == 0) atomicCAS(&s.ctl->err, 0, (int)DSSSP_ERR_OVERFLOW);
             return;
         }
     }
 }
 
-template <int DT>
-__global__ void k_na_unpack(NaArgs a) {
-    NaScratch *s = a.s;
-    if (na_vload(&s->ctl.err) != 0) return;            // outputs are written only on success
+template <int DT, typename RP>
+__global__ void k_na_unpack(NaArgs<RP> a) {
+    const NaMem &s = a.s;
+    if (na_vload(&s.ctl->err) != 0) return;            // outputs are written only on success
     for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.n; v += gridDim.x * blockDim.x) {
-        const unsigned long long p = s->packed[v];
+        const unsigned long long p = s.packed[v];
         const uint32_t k = (uint32_t)(p >> 32);
         if (DT == DSSSP_F32) ((float *)a.dist)[v] = __uint_as_float(k);
         else ((int32_t *)a.dist)[v] = (int32_t)k;
@@ -343,11 +340,53 @@ __global__ void k_na_unpack(NaArgs a) {
     }
 }
 
+template <int DT, typename RP>
+cudaError_t enqueue_dense(const NaArgs<RP> &a, int grid, cudaStream_t st) {
+    int init_grid = (int)((a.n > a.m ? a.n : a.m) / kNaBlock + 1);
+    if (init_grid > 4096) init_grid = 4096;
+    k_na_init<DT, RP><<<init_grid, kNaBlock, 0, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    void *args[] = {(void *)&a};
+    e = cudaLaunchCooperativeKernel((const void *)k_na_solve<DT, RP>, dim3(grid), dim3(kNaBlock), args, 0, st);
+    if (e != cudaSuccess) return e;
+    k_na_verify<DT, RP><<<grid, kNaBlock, 0, st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_na_unpack<DT, RP><<<(int)(a.n / kNaBlock + 1), kNaBlock, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Co-resident blocks of the dense solver on this device (both dtypes, both row types).
+int dense_grid(int dev) {
+    static std::mutex mu;
+    static int grid[64] = {};
+    if (dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (grid[dev] == 0) {
+        int sms = 0, lo = 1 << 30;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        const void *fns[] = {(const void *)k_na_solve<DSSSP_F32, int64_t>, (const void *)k_na_solve<DSSSP_I32, int64_t>,
+                             (const void *)k_na_solve<DSSSP_F32, uint32_t>, (const void *)k_na_solve<DSSSP_I32, uint32_t>};
+        for (const void *f : fns) {
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kNaBlock, 0) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            lo = per_sm < lo ? per_sm : lo;
+        }
+        grid[dev] = sms * lo;
+    }
+    return grid[dev];
+}
+
 // Device address of the scratch array, looked up once per device.
 constexpr int kMaxDevices = 64;
 std::mutex g_na_mutex;
 NaScratch *g_na_ptr[kMaxDevices] = {};
-int g_na_grid[kMaxDevices] = {};
 
 dsssp_status na_setup(int dev, NaScratch **ptr, int *grid) {
     if (dev < 0 || dev >= kMaxDevices) return DSSSP_ERR_UNSUPPORTED;
@@ -360,28 +399,47 @@ dsssp_status na_setup(int dev, NaScratch **ptr, int *grid) {
             cudaGetLastError();
             return DSSSP_ERR_CUDA;
         }
-        int sms = 0, per_sm = 0;
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_na_solve<DSSSP_F32>, kNaBlock, 0) != cudaSuccess) {
-            cudaGetLastError();
-            return DSSSP_ERR_CUDA;
-        }
-        int per_sm_i = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_i, k_na_solve<DSSSP_I32>, kNaBlock, 0) != cudaSuccess) {
-            cudaGetLastError();
-            return DSSSP_ERR_CUDA;
-        }
-        const int g = sms * (per_sm < per_sm_i ? per_sm : per_sm_i);
-        if (g < 1) return DSSSP_ERR_UNSUPPORTED;
-        g_na_grid[dev] = g;
         g_na_ptr[dev] = static_cast<NaScratch *>(p);
     }
     *ptr = g_na_ptr[dev];
-    *grid = g_na_grid[dev];
-    return DSSSP_OK;
+    *grid = dense_grid(dev);
+    return *grid > 0 ? DSSSP_OK : DSSSP_ERR_UNSUPPORTED;
 }
 
 }  // namespace
+
+namespace dsssp {
+
+cudaError_t dense_solve_launch(const uint32_t *off, const int32_t *col, const uint32_t *wbits, int dtype,
+                               uint32_t n, uint32_t m, uint32_t src, double delta, const NaMem &mem, void *dist,
+                               int32_t *pred, int64_t timeout_ns, int64_t max_phases, cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int grid = dense_grid(dev);
+    if (grid < 1) return cudaErrorNotSupported;
+    NaArgs<uint32_t> a{};
+    a.s = mem;
+    a.row_ptr = off;
+    a.col = col;
+    a.wbits = wbits;
+    a.dist = dist;
+    a.pred = pred;
+    a.delta = delta;
+    a.timeout_ns = timeout_ns;
+    a.max_phases = max_phases;
+    a.n = n;
+    a.m = m;
+    a.src = src;
+    a.light_max = light_max_key(dtype, delta);
+    a.nblocks = (uint32_t)grid;
+    a.validate = 0u;                  // the handle's CSR was validated at creation
+    if ((e = cudaMemsetAsync(mem.ctl, 0, sizeof(NaCtl), st)) != cudaSuccess) return e;
+    return dtype == DSSSP_F32 ? enqueue_dense<DSSSP_F32, uint32_t>(a, grid, st)
+                              : enqueue_dense<DSSSP_I32, uint32_t>(a, grid, st);
+}
+
+}  // namespace dsssp
 
 extern "C" dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t *row_ptr, const int32_t *col,
                                             const void *w, dsssp_dtype dtype, int32_t src, double delta,
@@ -403,8 +461,12 @@ extern "C" dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t 
     int grid = 0;
     dsssp_status st = na_setup(dev, &scratch, &grid);
     if (st != DSSSP_OK) return st;
-    NaArgs a{};
-    a.s = scratch;
+    NaArgs<int64_t> a{};
+    a.s.packed = scratch->packed;
+    a.s.fstamp = scratch->fstamp;
+    a.s.sstamp = scratch->sstamp;
+    a.s.far = scratch->far;
+    a.s.ctl = &scratch->ctl;
     a.row_ptr = row_ptr;
     a.col = col;
     a.wbits = static_cast<const uint32_t *>(w);
@@ -418,29 +480,11 @@ extern "C" dsssp_status dsssp_solve_noalloc(int64_t n, int64_t m, const int64_t 
     a.src = (uint32_t)src;
     a.light_max = light_max_key(dtype, delta);
     a.nblocks = (uint32_t)grid;
-    void *args[] = {&a};
-    const bool f32 = dtype == DSSSP_F32;
+    a.validate = 1u;
     // the previous call's control words, validation flags included, start at zero
     cudaError_t e = cudaMemsetAsync(&scratch->ctl, 0, sizeof(NaCtl), s);
-    if (e != cudaSuccess) { cudaGetLastError(); return DSSSP_ERR_CUDA; }
-    int init_grid = (int)((n > m ? n : m) / kNaBlock + 1);
-    if (init_grid > 4096) init_grid = 4096;
-    if (f32) k_na_init<DSSSP_F32><<<init_grid, kNaBlock, 0, s>>>(a);
-    else k_na_init<DSSSP_I32><<<init_grid, kNaBlock, 0, s>>>(a);
-    e = cudaGetLastError();
     if (e == cudaSuccess)
-        e = cudaLaunchCooperativeKernel(f32 ? (const void *)k_na_solve<DSSSP_F32> : (const void *)k_na_solve<DSSSP_I32>,
-                                        dim3(grid), dim3(kNaBlock), args, 0, s);
-    if (e == cudaSuccess) {
-        if (f32) k_na_verify<DSSSP_F32><<<grid, kNaBlock, 0, s>>>(a);
-        else k_na_verify<DSSSP_I32><<<grid, kNaBlock, 0, s>>>(a);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) {
-        if (f32) k_na_unpack<DSSSP_F32><<<(int)(n / kNaBlock + 1), kNaBlock, 0, s>>>(a);
-        else k_na_unpack<DSSSP_I32><<<(int)(n / kNaBlock + 1), kNaBlock, 0, s>>>(a);
-        e = cudaGetLastError();
-    }
+        e = dtype == DSSSP_F32 ? enqueue_dense<DSSSP_F32, int64_t>(a, grid, s) : enqueue_dense<DSSSP_I32, int64_t>(a, grid, s);
     int32_t err = 0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&err, &scratch->ctl.err, sizeof(err), cudaMemcpyDeviceToHost, s);

@@ -58,6 +58,7 @@ constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 #ifndef DSSSP_MIN_BLOCKS
 #define DSSSP_MIN_BLOCKS 2
 #endif
+
 constexpr int kIlp = DSSSP_ILP;        // independent 32-arc steps per warp iteration
 constexpr uint32_t kMinSlice = 32u;    // merge-path units of the smallest slice a warp takes
 #ifndef DSSSP_ENTRY_COST
@@ -75,7 +76,13 @@ struct BlockView {
     PhaseDesc d;
     uint32_t thr[kSlots + 1];
     int32_t err;            // the control block's error word when the view was taken
+    uint32_t gen;           // phase number of the view
+    uint32_t thr_epoch;     // window epoch of thr[] (re-read when the view's epoch differs)
 };
+
+// A bucket-slot stamp: one per (window, slot) of a solve, never 0 (the value
+// vertices start with). Windows are counted by the serial step (wepoch).
+__device__ __forceinline__ uint32_t slot_stamp(uint32_t wepoch, uint32_t t) { return ((wepoch << 5) | t) + 1u; }
 
 // ---------------------------------------------------------------------------
 // Per-warp staging of pushes in shared memory (wu::stage_*): a list counter,
@@ -252,7 +259,7 @@ __device__ __forceinline__ void queue_later(const SolveArgs &a, const BlockView 
                                             Push &p, uint32_t &ov_min) {
     if (ckey < bvw.thr[kSlots]) {
         const uint32_t t = slot_of(bvw.thr, ckey);
-        const uint32_t stamp = bvw.d.wbase32 + t + 1u;    // bucket + 1: one entry per (vertex, bucket)
+        const uint32_t stamp = slot_stamp(bvw.d.wepoch, t);   // one entry per (vertex, bucket)
         const uint32_t prev = atomicExch(a.b_stamp + v, stamp);
         const uint4 vi = __ldcs(a.vinfo + v);
         if (prev != stamp) {
@@ -558,6 +565,115 @@ __device__ void phase_rebin(const SolveArgs &a, const BlockView &bvw, BlockAcc &
 }
 
 // ---------------------------------------------------------------------------
+// The published view (Ctl::view): word l holds (phase number << 32) | field l.
+__device__ __forceinline__ uint32_t view_field(const PhaseDesc &d, int32_t err, uint32_t l) {
+    switch (l) {
+    case 0: return d.mode | (d.cur << 3) | (d.scur << 4) | (d.spush << 5) | (d.ov_cur << 6) | (d.solo << 7) |
+                   (d.slot << 8);
+    case 1: return d.sstamp;
+    case 2: return d.qstamp;
+    case 3: return d.T;
+    case 4: return d.T_lo;
+    case 5: return d.count;
+    case 6: return d.arcs;
+    case 7: return d.count2;
+    case 8: return d.count_h;
+    case 9: return d.arcs_h;
+    case 10: return d.wepoch;
+    case 11: return (uint32_t)err;
+    default: return 0u;
+    }
+}
+
+// Lane l of a warp stores field l of the published view into v (the lanes together fill it).
+__device__ __forceinline__ void view_store_field(BlockView &v, uint32_t l, uint32_t f, uint32_t gen) {
+    switch (l) {
+    case 0:
+        v.d.mode = f & 7u; v.d.cur = (f >> 3) & 1u; v.d.scur = (f >> 4) & 1u; v.d.spush = (f >> 5) & 1u;
+        v.d.ov_cur = (f >> 6) & 1u; v.d.solo = (f >> 7) & 1u; v.d.slot = (f >> 8) & 63u; v.gen = gen;
+        break;
+    case 1: v.d.sstamp = f; break;
+    case 2: v.d.qstamp = f; break;
+    case 3: v.d.T = f; break;
+    case 4: v.d.T_lo = f; break;
+    case 5: v.d.count = f; break;
+    case 6: v.d.arcs = f; break;
+    case 7: v.d.count2 = f; break;
+    case 8: v.d.count_h = f; break;
+    case 9: v.d.arcs_h = f; break;
+    case 10: v.d.wepoch = f; break;
+    case 11: v.err = (int32_t)f; break;
+    default: break;
+    }
+}
+
+__device__ __forceinline__ unsigned long long vload64(const unsigned long long *p) {
+    return *(const volatile unsigned long long *)p;
+}
+
+// Warp 0 of a block: take the published view into v once every word carries the
+// same phase number and that number is newer than `last` (0xFFFFFFFF: any).
+// Block 0 takes every view; the other blocks pass over solo views (block 0 runs
+// them alone) and wait for the next view with work for the whole grid, the end,
+// or an error. The wait gives up after timeout_ns without progress (a newer
+// view of any kind restarts the clock) or when the error word is set. The
+// window thresholds are re-read when the view's window epoch is not the one
+// v holds. Returns false on an error or a timeout.
+template <int DT>
+__device__ bool wait_view(const SolveArgs &a, uint32_t last, BlockView &v, bool patient) {
+    const uint32_t lane = lane_id();
+    Ctl *c = a.ctl;
+    uint64_t t0 = globaltimer();
+    uint32_t seen = last;
+    for (;;) {
+        const unsigned long long w = lane < (uint32_t)kViewWords ? vload64(&c->view[lane]) : 0ull;
+        const uint32_t g = (uint32_t)(w >> 32), f = (uint32_t)w;
+        const uint32_t g0 = __shfl_sync(FULL, g, 0);
+        const bool same = __all_sync(FULL, lane >= (uint32_t)kViewWords || g == g0);
+        const uint32_t f0 = __shfl_sync(FULL, f, 0), ferr = __shfl_sync(FULL, f, 11);
+        const bool newer = last == 0xFFFFFFFFu || (int32_t)(g0 - last) > 0;
+        if (same && newer) {
+            const bool solo = ((f0 >> 7) & 1u) != 0u;
+            if (blockIdx.x == 0 || !solo || (f0 & 7u) == MODE_DONE || ferr != 0u) {
+                __threadfence();                       // what the view's phase reads is visible
+                const uint32_t ep = __shfl_sync(FULL, f, 10);
+                const bool reload = __shfl_sync(FULL, lane == 0u && ep != v.thr_epoch, 0);
+                if (lane < (uint32_t)kViewWords) view_store_field(v, lane, f, g0);
+                if (reload) {
+                    v.thr[lane] = __ldcg(&c->thr[lane]);
+                    if (lane == 0u) {
+                        v.thr[kSlots] = __ldcg(&c->thr[kSlots]);
+                        v.thr_epoch = ep;
+                    }
+                }
+                __syncwarp();
+                return true;
+            }
+            patient = true;                            // a solo stretch: poll slowly
+        }
+        const uint64_t now = globaltimer();
+        if (same && g0 != seen) { seen = g0; t0 = now; }
+        int e = 0;
+        if (lane == 0u) e = vload(&c->err);
+        e = __shfl_sync(FULL, e, 0);
+        if (e != 0) {
+            if (lane == 0u) v.err = e;
+            __syncwarp();
+            return false;
+        }
+        if ((int64_t)(now - t0) > a.timeout_ns) {
+            if (lane == 0u) {
+                atomicCAS(&c->err, 0, (int)DSSSP_ERR_TIMEOUT);
+                v.err = (int32_t)DSSSP_ERR_TIMEOUT;
+            }
+            __syncwarp();
+            return false;
+        }
+        if (patient) __nanosleep(500);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Serial step: one warp, after every block has finished a phase. Every load is
 // in one batch: the serial state, the phase that ended and the list counters
 // (the same words on all lanes), and lane t's bucket slot t (its counters and
@@ -619,7 +735,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
     PhaseDesc nd{};
     nd.slot = kNoSlot;
     bool done = false;
-    if (s.phases >= a.max_phases) {
+    if (s.phases >= a.max_phases || s.wepoch >= (1u << 27) - 1u) {   // slot stamps hold 27 bits of epoch
         if (l0) {
             const int prev = atomicCAS(&c->err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
             err = prev != 0 ? prev : (int)DSSSP_ERR_NOT_CONVERGED;
@@ -720,13 +836,17 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
             // lane t resets slot t and sets its threshold, lane 0 also the window's end
             c->ctrSL[lane] = 0ull;
             c->nSH[lane] = 0u;
+            s.wepoch += 1u;
             if (ov_min < inf_key<DT>()) {
+                // bucket indices saturate at INT64_MAX (a tiny Delta against large
+                // distances): every such key then belongs to the window's slot 0
                 const int64_t w = bucket_of_key(ov_min, DT, a.delta);
                 s.wbase = w;
                 s.bucket = w - 1;
-                my_th = w + lane < INT64_MAX ? bucket_floor_key(w + lane, DT, a.delta) : inf_key<DT>();
+                my_th = (int64_t)lane <= INT64_MAX - w ? bucket_floor_key(w + lane, DT, a.delta) : inf_key<DT>();
+                if (lane == 0u && my_th > ov_min) my_th = ov_min;         // slot 0 starts at or below the smallest key
                 if (lane == 1u && my_th <= ov_min) my_th = ov_min + 1u;   // the smallest key lands in slot 0
-                th_end = w + kSlots < INT64_MAX ? bucket_floor_key(w + kSlots, DT, a.delta) : inf_key<DT>();
+                th_end = (int64_t)kSlots <= INT64_MAX - w ? bucket_floor_key(w + kSlots, DT, a.delta) : inf_key<DT>();
             } else {                               // only stale entries remain: drop them all
                 my_th = inf_key<DT>();
                 th_end = inf_key<DT>();
@@ -753,7 +873,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
     nd.T = s.T;
     nd.T_lo = nd.slot < kNoSlot ? s.T_lo : 0u;
     nd.ov_cur = s.ov_cur;
-    nd.wbase32 = (uint32_t)s.wbase;
+    nd.wepoch = s.wepoch;
     // little work: one block runs the phase without a grid-wide barrier
     const uint32_t work = next_mode == MODE_REBIN ? nd.count
                                                   : max(nd.arcs + nd.arcs_h, nd.count + nd.count2 + nd.count_h);
@@ -768,25 +888,21 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
         #pragma unroll
         for (int k = 0; k < kDescVec; ++k) dd[k] = ds[k];
     }
+    // publish: everything above (every lane's writes) reaches memory before any view word
+    const uint32_t gen = (uint32_t)s.phases;
+    __threadfence();
+    __syncwarp();
+    if (lane < (uint32_t)kViewWords)
+        *(volatile unsigned long long *)&c->view[lane] = ((unsigned long long)gen << 32) | view_field(nd, err, lane);
     if (out != nullptr) {
         out->thr[lane] = my_th;
         if (l0) {
             out->thr[kSlots] = th_end;
             out->d = nd;
             out->err = err;
+            out->gen = gen;
+            out->thr_epoch = s.wepoch;
         }
-    }
-}
-
-// Every thread of the block calls it; fills the block's view of the phase.
-__device__ __forceinline__ void read_view(const Ctl *c, BlockView &v) {
-    for (uint32_t i = threadIdx.x; i < (uint32_t)kDescVec + kSlots + 2u; i += blockDim.x) {
-        if (i < (uint32_t)kDescVec)
-            reinterpret_cast<uint4 *>(&v.d)[i] = __ldcg(reinterpret_cast<const uint4 *>(&c->desc) + i);
-        else if (i < (uint32_t)kDescVec + kSlots + 1u)
-            v.thr[i - kDescVec] = __ldcg(&c->thr[i - kDescVec]);
-        else
-            v.err = __ldcg(&c->err);
     }
 }
 
@@ -812,63 +928,42 @@ __device__ __forceinline__ void acc_init(BlockAcc &acc) {
     acc.arcs_light = acc.arcs_heavy = acc.improvements = acc.far_scanned = 0;
 }
 
-// Grid-wide barrier with a serial step, every wait bounded by timeout_ns.
-// Warp 0 of every block arrives; in the last block to arrive it runs the serial
-// step. With run_serial false (after a solo stretch, whose serial steps block 0
-// already ran) the last arrival only releases; blocks that wait through a solo
-// stretch poll slowly so that they do not load the L2 the solo block uses.
-// Returns false when this block saw the error word set or gave up waiting; the
-// error word is otherwise checked in the next view.
+// Grid-wide barrier with a serial step. Warp 0 of every block arrives; in the
+// last block to arrive it runs the serial step, which publishes the next view
+// (and writes it into that block's own view). The others wait for the view in
+// wait_view, bounded by timeout_ns. A solo view goes to block 0 alone: a last
+// arrival that is not block 0 then waits like the others. Returns false when
+// the block saw the error word set or gave up waiting.
 template <int DT>
-__device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, int *s_ok, bool run_serial, bool patient) {
+__device__ bool grid_barrier(const SolveArgs &a, BlockAcc &acc, BlockView &view, int *s_ok) {
     __syncthreads();
     if (threadIdx.x < 32u) {
         const uint32_t lane = threadIdx.x;
         Ctl *c = a.ctl;
-        unsigned gen = 0u, arrived = 0u;
+        const uint32_t my_gen = view.gen;
+        unsigned arrived = 0u;
         if (lane == 0u) {
             flush_ov_min(c, acc, inf_key<DT>());
             __threadfence();
-            gen = vload(&c->bar_gen);
             arrived = atomicAdd(&c->bar_count, 1u);
-            if (run_serial && arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
+            if (arrived == 0u) c->t_first = globaltimer();   // phase-time diagnostics
         }
         arrived = __shfl_sync(FULL, arrived, 0);
-        int ok = 1;
+        bool ok = true;
         if (arrived == a.nblocks - 1u) {
             if (lane == 0u) {
                 atomicExch(&c->bar_count, 0u);
                 __threadfence();
             }
             __syncwarp();
-            if (run_serial) serial_step<DT>(a, nullptr);
+            serial_step<DT>(a, &view);
             __syncwarp();
-            if (lane == 0u) {
-                __threadfence();
-                atomicExch(&c->bar_gen, gen + 1u);
-            }
-        } else if (lane == 0u) {
-            // bounded wait: timeout_ns without progress (a solo block's serial
-            // steps advance ss.phases, which restarts the clock)
-            uint64_t t0 = globaltimer();
-            int64_t seen = patient ? vload(&c->ss.phases) : 0;
-            while (vload(&c->bar_gen) == gen) {
-                if (vload(&c->err) != 0) { ok = 0; break; }
-                const uint64_t now = globaltimer();
-                if (patient) {
-                    const int64_t ph = vload(&c->ss.phases);
-                    if (ph != seen) { seen = ph; t0 = now; }
-                }
-                if ((int64_t)(now - t0) > a.timeout_ns) {
-                    atomicCAS(&c->err, 0, (int)DSSSP_ERR_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                if (patient) __nanosleep(500);
-            }
-            __threadfence();
+            if (blockIdx.x != 0 && view.d.solo != 0u && view.d.mode != MODE_DONE && view.err == 0)
+                ok = wait_view<DT>(a, view.gen, view, true);
+        } else {
+            ok = wait_view<DT>(a, my_gen, view, false);
         }
-        if (lane == 0u) *s_ok = ok;
+        if (lane == 0u) *s_ok = ok && view.err == 0;
     }
     __syncthreads();
     return *s_ok != 0;
@@ -923,25 +1018,28 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(Solv
     __shared__ BlockAcc acc;
     __shared__ int s_ok;
     if (a.test_hook == DSSSP_HOOK_STALL_BARRIER && blockIdx.x == 1) return;
-    if (threadIdx.x == 0) acc_init<DT>(acc);
+    if (threadIdx.x == 0) {
+        acc_init<DT>(acc);
+        view.thr_epoch = 0xFFFFFFFFu;
+        view.err = 0;
+    }
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
-    bool have_view = false;
-    for (;;) {
-        if (!have_view) {
-            read_view(a.ctl, view);
-            __syncthreads();
-        }
-        have_view = false;
+    __syncthreads();
+    if (threadIdx.x < 32u) {
+        const bool ok = wait_view<DT>(a, 0xFFFFFFFFu, view, false);
+        if (threadIdx.x == 0u) s_ok = ok;
+    }
+    __syncthreads();
+    while (s_ok) {
         if (view.err != 0 || view.d.mode == MODE_DONE) break;
         // A solo phase (little work) runs on block 0 only: its phases follow each
-        // other with block-level synchronisation and the serial step in warp 0,
-        // while the other blocks wait in the grid barrier until a phase with work
-        // for the whole grid (or the end) comes.
+        // other with block-level synchronisation and the serial step in warp 0;
+        // the other blocks wait for the next view with work for the whole grid.
         const bool solo = view.d.solo != 0u;
-        if (!solo || blockIdx.x == 0) run_phase<DT>(a, view, acc, slot, stage, solo ? wib : gw, solo ? nwb : nw);
-        if (solo && blockIdx.x == 0) {
+        run_phase<DT>(a, view, acc, slot, stage, solo ? wib : gw, solo ? nwb : nw);
+        if (solo) {
             __threadfence();             // list entries and flags reach L2 before the serial step reads them
             __syncthreads();
             if (threadIdx.x < 32u) {     // warp 0: the serial step, which also writes the block's next view
@@ -951,19 +1049,11 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_solve_persistent(Solv
                 }
                 __syncwarp();
                 serial_step<DT>(a, &view);
-                __syncwarp();
-                if (threadIdx.x == 0u) __threadfence();
             }
             __syncthreads();
-            if (view.err != 0) break;
-            have_view = true;
-            if (view.d.solo && view.d.mode != MODE_DONE) continue;   // next solo phase right away
-            if (!grid_barrier<DT>(a, acc, &s_ok, false, false)) break;   // release the waiting blocks
-        } else if (solo) {
-            if (!grid_barrier<DT>(a, acc, &s_ok, false, true)) break;
-        } else {
-            if (!grid_barrier<DT>(a, acc, &s_ok, true, false)) break;
+            continue;
         }
+        if (!grid_barrier<DT>(a, acc, view, &s_ok)) break;
     }
     __syncthreads();
     if (vload(&a.ctl->ovf) != 0u && vload(&a.ctl->err) == 0) verify_overflow<DT>(a, gw, nw);
@@ -977,10 +1067,16 @@ __global__ void __launch_bounds__(512, DSSSP_MIN_BLOCKS) k_phase(SolveArgs a) {
     WarpStage *stage = reinterpret_cast<WarpStage *>(dyn_smem);
     __shared__ BlockView view;
     __shared__ BlockAcc acc;
-    read_view(a.ctl, view);
+    if (threadIdx.x < 32u) {                  // the view k_serial (or k_init) published
+        const uint32_t lane = threadIdx.x;
+        const unsigned long long w = lane < (uint32_t)kViewWords ? vload64(&a.ctl->view[lane]) : 0ull;
+        if (lane < (uint32_t)kViewWords) view_store_field(view, lane, (uint32_t)w, (uint32_t)(w >> 32));
+        view.thr[lane] = __ldcg(&a.ctl->thr[lane]);
+        if (lane == 0u) view.thr[kSlots] = __ldcg(&a.ctl->thr[kSlots]);
+    }
     if (threadIdx.x == 0) acc_init<DT>(acc);
     __syncthreads();
-    if (view.d.mode != MODE) return;
+    if (view.d.mode != MODE || view.err != 0) return;
     run_phase<DT>(a, view, acc, slot, stage, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
                   (gridDim.x * blockDim.x) >> 5);
     __syncthreads();
@@ -1020,7 +1116,6 @@ __global__ void k_init(SolveArgs a) {
         Ctl *c = a.ctl;
         const uint4 vs = a.vinfo[a.src];
         c->bar_count = 0u;
-        c->bar_gen = 0u;
         c->err = 0;
         c->ovf = 0u;
         c->t_first = 0ull;
@@ -1052,6 +1147,7 @@ __global__ void k_init(SolveArgs a) {
         d.arcs = (uint32_t)c->ctrF[0];
         d.solo = d.arcs <= a.solo_work ? 1u : 0u;
         c->desc = d;
+        for (uint32_t l = 0; l < (uint32_t)kViewWords; ++l) c->view[l] = view_field(d, 0, l);   // phase 0
         a.F0[0] = make_uint2(a.src, 0u);
         a.S0[0] = make_uint2(a.src, 0u);
     }
@@ -1103,8 +1199,9 @@ cudaError_t allow_stage_smem() {
         (const void *)k_phase<DSSSP_F32, MODE_HEAVY>, (const void *)k_phase<DSSSP_I32, MODE_HEAVY>,
         (const void *)k_phase<DSSSP_F32, MODE_REBIN>, (const void *)k_phase<DSSSP_I32, MODE_REBIN>,
         (const void *)k_phase<DSSSP_F32, MODE_FUSED>, (const void *)k_phase<DSSSP_I32, MODE_FUSED>};
-    for (const void *f : fns)
+    for (const void *f : fns) {
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess) return e;
+    }
     if (dev >= 0 && dev < 64) done[dev] = true;
     return cudaSuccess;
 }

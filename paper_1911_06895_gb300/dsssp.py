@@ -42,6 +42,7 @@ DSSSP_I32 = 0
 DSSSP_F32 = 1
 DSSSP_MODE_PERSISTENT = 0
 DSSSP_MODE_STEPPED = 1
+DSSSP_MODE_DENSE = 2
 DSSSP_FLAG_ASYNC = 0x1
 DSSSP_FLAG_NO_FUSE = 0x2
 DSSSP_HOOK_NONE = 0

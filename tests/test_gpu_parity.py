@@ -50,8 +50,9 @@ def assert_same(g, src, d, p, d_ref=None, p_ref=None, what=""):
     assert badp.size == 0, f"{what}: {badp.size} predecessors differ, first {badp[:5]} gpu {p[badp[:5]]} ref {p_ref[badp[:5]]}"
 
 
-# persistent, stepped, a small grid, and heavy passes kept apart from the next bucket (DSSSP_FLAG_NO_FUSE)
-MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64), dict(flags=2)]
+# persistent, stepped, a small grid, heavy passes kept apart from the next bucket (DSSSP_FLAG_NO_FUSE),
+# and the full-vector form (DSSSP_MODE_DENSE)
+MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64), dict(flags=2), dict(mode=2)]
 
 
 # ------------------------------------------------------------------ hand-built cases
@@ -129,6 +130,27 @@ def test_edge_cases(ds):
         h.close()
 
 
+def test_huge_bucket_indices(ds):
+    """Bucket indices past 2^32 and past INT64_MAX (a small Delta against large distances):
+    every vertex is still processed. int32: key 1431655765 at Delta 1/3 is bucket 2^32 - 1;
+    float32: 1e9 at Delta 1e-12 is bucket 1e21, which saturates."""
+    cases = [
+        (graphgen.from_arcs(4, [(0, 1), (1, 2), (0, 3)], np.array([1431655765, 5, 7], np.int32), dtype=np.int32),
+         [1.0 / 3.0, 0.25, 0.1]),
+        (graphgen.from_arcs(4, [(0, 1), (1, 2), (2, 3)], np.array([1e9, 1.0, 3e9], np.float32), dtype=np.float32),
+         [1e-12, 1e-3, 1e-30]),
+    ]
+    for g, deltas in cases:
+        h = ds.Graph(g.row_ptr, g.col, g.w)
+        d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
+        assert (p_ref >= 0).all()
+        for delta in deltas:
+            for opt in MODES:
+                d, p, _ = gpu_solve(ds, h, 0, delta, **opt)
+                assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta} {opt}")
+        h.close()
+
+
 def overflow_cases():
     """(graph, source, overflows?) -- reading R14: an overflow is a sum out of a reached
     vertex, at its final distance, that the weight type cannot hold."""
@@ -191,7 +213,7 @@ def test_rmat14_int_delta32(ds):
     for opt in MODES + [dict(grid_size=1), dict(block_size=128), dict(grid_size=7, block_size=32)]:
         d, p, st = gpu_solve(ds, h, srcs[0], deltas[0], **opt)
         assert_same(g, srcs[0], d, p, d_ref, p_ref, str(opt))
-        assert st["buckets"] >= 1 and st["arcs_light"] > 0
+        assert st["buckets"] >= 1 and (st["arcs_light"] > 0 or (opt.get("mode") == 2 and st["light_phases"] > 0))
     # the other sources too
     for s in graphgen.random_sources(g, 6, 99):
         d, p, _ = gpu_solve(ds, h, int(s), deltas[0])
@@ -344,6 +366,17 @@ def test_full_rmat22_every_source_every_delta_exact(ds, rmat22):
             for delta in deltas:
                 d, p, _ = gpu_solve(ds, h, s, delta)
                 assert_same(g, s, d, p, d_ref, p_ref, f"source {s} delta {delta}")
+
+
+def test_full_rmat22_dense_vector_form_exact(ds, rmat22):
+    """The paper's full-vector form (DSSSP_MODE_DENSE) at full size: two sources, every Delta."""
+    g, srcs, deltas, h = rmat22
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, srcs[:2])
+    for s, d_ref, p_ref in zip(srcs[:2], refd, refp):
+        for delta in deltas:
+            d, p, st = gpu_solve(ds, h, s, delta, mode=2)
+            assert_same(g, s, d, p, d_ref, p_ref, f"dense source {s} delta {delta}")
+            assert st["light_phases"] > 0 and st["heavy_phases"] > 0
 
 
 def test_full_grid4096_all_deltas_exact(ds):
