@@ -107,8 +107,10 @@ typedef struct {
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
-    int32_t  team_blocks;   /* batches: blocks per instance (a thread-block cluster of 1, 2, 4 or 8);
-                               0 = automatic (more blocks per instance when instances are few)   */
+    int32_t  team_blocks;   /* batches: blocks per instance (a thread-block cluster of 1, 2, 4, 8 or
+                               16; 16 is a non-portable cluster size, UNSUPPORTED where it cannot
+                               be co-scheduled); 0 = automatic (1-8: more blocks per instance when
+                               instances are few)                                               */
     int32_t  reserved[4];
 } dsssp_options;
 
@@ -272,7 +274,7 @@ typedef struct {
  *   opt         NULL, or options (block_size must be 512 or 0; grid_size caps the number of
  *               blocks; max_phases caps the phases of each instance; team_blocks sets how many
  *               blocks -- a thread-block cluster sharing the instance's control through
- *               distributed shared memory -- solve one instance: 1, 2, 4, 8, or 0 for automatic);
+ *               distributed shared memory -- solve one instance: 1, 2, 4, 8, 16, or 0 for automatic);
  *   stream      orders the set-up work (light/heavy splits, tables); the call waits for it;
  *   out         receives the plan.
  * The plan keeps the graphs' splits for these Deltas alive (a graph holds at most four) and
@@ -367,8 +369,8 @@ dsssp_status dsssp_autotune(dsssp_graph *const *graphs, int32_t n_graphs, const 
 dsssp_status dsssp_tune_solo_work(dsssp_graph *g, const int32_t *sample_src, int32_t k, double delta,
                                   int32_t *solo_work_out, double *ms_out, void *stream);
 
-/* Choose the team size of a batch (dsssp_options.team_blocks: blocks per instance, 1, 2, 4 or
- * 8) by timing the whole batch at each size: builds the plan the arguments describe (as
+/* Choose the team size of a batch (dsssp_options.team_blocks: blocks per instance, 1, 2, 4, 8
+ * or 16; sizes that cannot be co-scheduled are skipped) by timing the whole batch at each size: builds the plan the arguments describe (as
  * dsssp_batch_create, outputs written) once per size, runs it twice and keeps the fastest
  * second run. team_blocks_out receives the size; ms_out (may be NULL) its device time.
  * Waits for its work. Errors: those of dsssp_batch_create / run / sync. */

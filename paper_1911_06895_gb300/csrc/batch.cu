@@ -985,7 +985,16 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
     if (bps < 1) return fail(DSSSP_ERR_UNSUPPORTED);
     const long long blocks_max = (long long)bps * sms;
     int csize = o.team_blocks;
-    if (csize != 0 && csize != 1 && csize != 2 && csize != 4 && csize != 8) return fail(DSSSP_ERR_INVALID_ARG);
+    if (csize != 0 && csize != 1 && csize != 2 && csize != 4 && csize != 8 && csize != 16)
+        return fail(DSSSP_ERR_INVALID_ARG);
+    if (csize == 16) {           // clusters above 8 blocks are opt-in per kernel
+        if (cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess ||
+            cudaFuncSetAttribute((const void *)k_backward, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            return fail(DSSSP_ERR_UNSUPPORTED);
+        }
+    }
     if (csize == 0) {            // largest power of two <= 8 with instances x team blocks <= 2 x resident blocks
         csize = 1;
         while (csize < 8 && (long long)n_inst * csize <= blocks_max) csize *= 2;
