@@ -411,8 +411,12 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
         // window: lane k holds entry jw + k; wend = arc offset just past the window.
         // A stale slot entry (its vertex moved to a lower bucket) gets key INF and is skipped.
         uint32_t jw = lo, wv = 0, woff = 0xFFFFFFFFu, wbeg = 0, wkey = inf_key<DT>(), wend = 0;
-        auto load_window = [&](uint32_t j) {
+        // The arcs of stale entries in this warp's slice are taken off the count of
+        // relaxed arcs when the window is loaded (`from`: entries starting before it
+        // were counted with an earlier window).
+        auto load_window = [&](uint32_t j, uint32_t from) {
             const uint32_t idx = j + lane;
+            bool stale = false;
             if (idx < count) {
                 const uint2 en = __ldcs(list + idx);
                 wv = en.x < a.n ? en.x : 0u;          // defensive: ids come from device lists
@@ -420,13 +424,23 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
                 const uint32_t k = (uint32_t)(__ldcg(a.packed + wv) >> 32);
                 const uint4 vi = __ldcs(a.vinfo + wv);
                 wbeg = LIGHT ? vi.x : vi.y;
-                wkey = (T_lo == 0u || k >= T_lo) ? k : inf_key<DT>();
+                stale = T_lo != 0u && k < T_lo;
+                wkey = stale ? inf_key<DT>() : k;
             } else {
                 wv = 0; woff = 0xFFFFFFFFu; wbeg = 0; wkey = inf_key<DT>();
             }
             wend = (j + 32u < count) ? __ldcg(offs + 2ull * (j + 32u)) : E;
+            if (T_lo != 0u) {
+                uint32_t nxt = __shfl_down_sync(FULL, woff, 1);
+                if (idx + 1u >= count) nxt = E;
+                else if (lane == 31u) nxt = wend;
+                const uint32_t lo_a = max(woff, e0), hi_a = min(nxt, e1);
+                uint32_t skip = (stale && woff >= from && hi_a > lo_a) ? hi_a - lo_a : 0u;
+                skip = __reduce_add_sync(FULL, skip);
+                if (lane == 0u && skip) atomicAdd(&acc.arcs_light, 0ull - (unsigned long long)skip);
+            }
         };
-        load_window(jw);
+        load_window(jw, 0u);
         int *sl = slot + (threadIdx.x >> 5) * 32;
         // Each iteration maps kIlp 32-arc steps to owners first, then issues their
         // arc loads, distance reads and atomics back to back.
@@ -446,7 +460,7 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
                         // move the window to the owner of `base` (inside it, or the entry just past it)
                         const uint32_t shift = base >= wend ? 32u : 31u - __clz(__ballot_sync(FULL, woff <= base));
                         jw += shift;
-                        load_window(jw);
+                        load_window(jw, base);
                     }
                     // owner of arc base + lane: the last window entry starting at or before it
                     const int carry = 31 - __clz(__ballot_sync(FULL, woff <= base));
