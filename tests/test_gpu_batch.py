@@ -98,7 +98,7 @@ def test_one_team_reuses_its_memory(ds):
     b.close()
 
 
-@pytest.mark.parametrize("team_blocks", [1, 2, 4, 8])
+@pytest.mark.parametrize("team_blocks", [1, 2, 4, 8, 16])
 def test_cluster_teams(ds, team_blocks):
     """An instance solved by a cluster of blocks sharing its control through distributed
     shared memory gives the same bits; few teams force several instances per team."""
@@ -138,12 +138,13 @@ def test_cluster_teams_tape_and_graphs(ds):
     g, sources, _ = W.rmat20_lognormal(scale=13, n_sources=6)
     cs = [graphgen.random_costs(g.n, 70 + k) for k in range(len(sources))]
     h = ds.Graph(g.row_ptr, g.col, g.w)
-    b = batch(ds, h, [0.7], sources, tape=True, team_blocks=4)
-    b.run()
-    b.sync()
     ref = oracle.tree_gradient_many(g.row_ptr, g.col, g.w, sources, cs)
-    assert_grad_close(gpu_grad(ds, b, cs, g.m), ref, "cluster tape")
-    b.close()
+    for tb in (4, 16):                          # 16: a non-portable cluster size, forward and adjoint
+        b = batch(ds, h, [0.7], sources, tape=True, team_blocks=tb)
+        b.run()
+        b.sync()
+        assert_grad_close(gpu_grad(ds, b, cs, g.m), ref, f"cluster tape {tb}")
+        b.close()
     fam = W.er_family(count=10, n_lo=200, n_hi=30000)
     hs = [ds.Graph(x.row_ptr, x.col, x.w) for x, _ in fam]
     b = batch(ds, hs, [0.2] * len(fam), [s for _, s in fam], src_graph=list(range(len(fam))), team_blocks=2)
