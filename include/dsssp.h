@@ -75,12 +75,20 @@ typedef struct dsssp_graph dsssp_graph;
 typedef enum {
     DSSSP_MODE_PERSISTENT = 0,   /* one cooperative kernel runs every phase; grid-wide barriers  */
     DSSSP_MODE_STEPPED = 1,      /* one kernel launch per phase, loop driven by the host          */
-    DSSSP_MODE_DENSE = 2         /* the paper's full-vector form (Fig. 1 left; the filter fusion of
+    DSSSP_MODE_DENSE = 2,        /* the paper's full-vector form (Fig. 1 left; the filter fusion of
                                     Section VI-B): t_Bi, S and the far pile are per-vertex stamps,
                                     every phase scans all n of them and filters each scanned row
                                     into light or heavy arcs on the fly. Same results; block_size,
                                     grid_size, solo_work, flags other than ASYNC and test_hook are
                                     ignored; stats fill buckets, light_phases and heavy_phases. */
+    DSSSP_MODE_TEAM = 3          /* the solve as one instance of the batch kernel on a single
+                                    thread-block cluster of dsssp_options.team_blocks blocks (0: 16, or 8
+                                    where 16 cannot be scheduled): phases end in a hardware cluster
+                                    barrier and the control stays in shared memory, which suits graphs
+                                    with many small phases (high diameter, small frontiers). Same
+                                    results; block_size, grid_size, solo_work, timeout_ns and test_hook
+                                    are ignored; stats fill the phase, arc and vertex counters,
+                                    rebin_phases = next-bucket selections, ns_total, grid_size = blocks */
 } dsssp_mode;
 
 /* dsssp_options.flags */
@@ -107,10 +115,11 @@ typedef struct {
     int64_t  max_phases;    /* cap on phases (barrier steps); default 2^26                       */
     int64_t  timeout_ns;    /* limit of any single device-side wait; default 2e9 (2 s)           */
     int32_t  test_hook;     /* DSSSP_HOOK_*                                                      */
-    int32_t  team_blocks;   /* batches: blocks per instance (a thread-block cluster of 1, 2, 4, 8 or
-                               16; 16 is a non-portable cluster size, UNSUPPORTED where it cannot
-                               be co-scheduled); 0 = automatic (1-8: more blocks per instance when
-                               instances are few)                                               */
+    int32_t  team_blocks;   /* batches and DSSSP_MODE_TEAM solves: blocks per instance (a
+                               thread-block cluster of 1, 2, 4, 8 or 16; 16 is a non-portable
+                               cluster size, UNSUPPORTED where it cannot be co-scheduled);
+                               0 = automatic (batches: 1-8, more blocks per instance when
+                               instances are few; team solves: 16, else 8)                        */
     int32_t  reserved[4];
 } dsssp_options;
 
@@ -368,6 +377,16 @@ dsssp_status dsssp_autotune(dsssp_graph *const *graphs, int32_t n_graphs, const 
  * Errors: INVALID_ARG and those of dsssp_solve. */
 dsssp_status dsssp_tune_solo_work(dsssp_graph *g, const int32_t *sample_src, int32_t k, double delta,
                                   int32_t *solo_work_out, double *ms_out, void *stream);
+
+/* Choose the scheme of single solves of one graph at one Delta: times k sample solves in the
+ * persistent mode at the solo thresholds of dsssp_tune_solo_work and in DSSSP_MODE_TEAM with 8 and
+ * 16 blocks (a size that cannot be scheduled here is skipped), and writes to *opt_out the default
+ * options with the fastest scheme's mode, solo_work and team_blocks; ms_out (may be NULL) receives
+ * its device time. The paper fixes no schedule (Section VI); delta-stepping phases are small on
+ * high-diameter graphs and large on small-world ones, which favours one scheme or the other.
+ * Waits for its work. Errors: INVALID_ARG and those of dsssp_solve. */
+dsssp_status dsssp_tune_schedule(dsssp_graph *g, const int32_t *sample_src, int32_t k, double delta,
+                                 dsssp_options *opt_out, double *ms_out, void *stream);
 
 /* Choose the team size of a batch (dsssp_options.team_blocks: blocks per instance, 1, 2, 4, 8
  * or 16; sizes that cannot be co-scheduled are skipped) by timing the whole batch at each size: builds the plan the arguments describe (as

@@ -99,6 +99,7 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     const size_t o_ov1 = bytes;    bytes += up(n * 4);
     const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
     const size_t o_nactl = bytes;  bytes += up(sizeof(NaCtl));
+    const size_t o_team = bytes;   bytes += up(team_region_bytes());
     const size_t o_sticky = bytes; bytes += up(sizeof(int32_t));
     char *base = nullptr;
     DSSSP_TRY(cudaMalloc(&base, bytes));
@@ -123,6 +124,7 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     a.ctl = (Ctl *)(base + o_ctl);
     g->ctl = a.ctl;
     g->nactl = (NaCtl *)(base + o_nactl);
+    g->team_region = base + o_team;
     g->sticky = (int32_t *)(base + o_sticky);
     return DSSSP_OK;
 }
@@ -286,10 +288,15 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
         if (opt_in->max_phases) opt.max_phases = opt_in->max_phases;
         if (opt_in->timeout_ns) opt.timeout_ns = opt_in->timeout_ns;
         opt.test_hook = opt_in->test_hook;
+        opt.team_blocks = opt_in->team_blocks;
     }
     if (opt.block_size < 32 || opt.block_size > 512 || opt.block_size % 32 != 0) return DSSSP_ERR_INVALID_ARG;
     if (opt.max_phases < 1 || opt.timeout_ns < 1 || opt.grid_size < 0) return DSSSP_ERR_INVALID_ARG;
-    if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED && opt.mode != DSSSP_MODE_DENSE)
+    if (opt.mode != DSSSP_MODE_PERSISTENT && opt.mode != DSSSP_MODE_STEPPED && opt.mode != DSSSP_MODE_DENSE &&
+        opt.mode != DSSSP_MODE_TEAM)
+        return DSSSP_ERR_INVALID_ARG;
+    if (opt.team_blocks != 0 && opt.team_blocks != 1 && opt.team_blocks != 2 && opt.team_blocks != 4 &&
+        opt.team_blocks != 8 && opt.team_blocks != 16)
         return DSSSP_ERR_INVALID_ARG;
     DeviceGuard dg(g->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -327,6 +334,38 @@ dsssp_status dsssp_solve(dsssp_graph *g, int32_t src, double delta, void *dist, 
     dsssp_status rc = ensure_split(g, delta, st, &sp);
     if (rc != DSSSP_OK) return rc;
     if ((rc = ensure_workspace(g)) != DSSSP_OK) return rc;
+
+    if (opt.mode == DSSSP_MODE_TEAM) {
+        // one instance of the batch kernel on one thread-block cluster (16 blocks unless
+        // asked otherwise; 8 where a 16-block cluster cannot be scheduled)
+        int tb = opt.team_blocks ? opt.team_blocks : 16;
+        cudaError_t e = team_solve_launch(g, sp, src, delta, dist, pred, tb, opt.max_phases, st);
+        if (e != cudaSuccess && opt.team_blocks == 0) {
+            cudaGetLastError();
+            tb = 8;
+            e = team_solve_launch(g, sp, src, delta, dist, pred, tb, opt.max_phases, st);
+        }
+        DSSSP_TRY(e);
+        k_sticky<<<1, 1, 0, st>>>(team_err(g), g->sticky);
+        DSSSP_TRY(cudaGetLastError());
+        if ((opt.flags & DSSSP_FLAG_ASYNC) && !stats) return DSSSP_OK;
+        int herr = 0;
+        long long hst[kTeamStatsCount];
+        DSSSP_TRY(cudaMemcpyAsync(&herr, team_err(g), sizeof(int), cudaMemcpyDeviceToHost, st));
+        DSSSP_TRY(cudaMemcpyAsync(hst, team_stats(g), sizeof(hst), cudaMemcpyDeviceToHost, st));
+        DSSSP_TRY(cudaStreamSynchronize(st));
+        if (stats) {
+            std::memset(stats, 0, sizeof *stats);
+            team_stats_to_solve(hst, stats);
+            stats->grid_size = tb;
+            stats->block_size = 512;
+        }
+        if (herr != 0) {
+            cudaMemsetAsync(g->sticky, 0, sizeof(int32_t), st);
+            return (dsssp_status)herr;
+        }
+        return DSSSP_OK;
+    }
 
     // grid: all co-resident blocks (the persistent kernel waits on every block)
     if (g->occ_block != opt.block_size) {

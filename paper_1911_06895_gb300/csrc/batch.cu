@@ -139,6 +139,7 @@ struct TeamShared {
     uint32_t next_min;                       // SELECT: smallest key kept
     uint32_t ovf;                            // a relaxation met a sum the weight type cannot hold
     uint32_t ovf_bad;                        // the final check confirmed an overflow
+    uint32_t capped;                         // the instance reached the phase cap (no result)
     uint32_t mode, cur, scur, xcur, pstamp, sst, T, T_lo, fst, gen, inst;
     uint32_t gen_seen;                       // every block: the leader's generator at instance start
 };
@@ -489,6 +490,7 @@ __device__ __noinline__ void team_decide(TeamShared &s, const BGraphDev &g, cons
     s.phases += 1;
     if (s.phases >= a.max_phases) {
         atomicCAS(a.err, 0, (int)DSSSP_ERR_NOT_CONVERGED);
+        s.capped = 1u;
         s.mode = T_DONE;
         return;
     }
@@ -625,6 +627,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             s.next_min = inf_key<DT>();
             s.ovf = 0u;
             s.ovf_bad = 0u;
+            s.capped = 0u;
             s.cur = s.scur = s.xcur = 0u;
             s.fst = ++s.gen;
             s.sst = ++s.gen;
@@ -682,9 +685,14 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
         // cannot hold, every arc of every reached vertex is tested again with its
         // final distance (one warp per vertex); a confirmed overflow fails the
         // batch with DSSSP_ERR_OVERFLOW and leaves this instance's outputs alone.
-        bool write_out = true;
-        if (tid == 0) s.ovf = cl.map_shared_rank(&s, 0)->ovf;   // same value in every block of the team
+        // An instance that reached the phase cap has no result either.
+        if (tid == 0) {
+            const TeamShared *L = cl.map_shared_rank(&s, 0);   // same values in every block of the team
+            s.ovf = L->ovf;
+            s.capped = L->capped;
+        }
         __syncthreads();
+        bool write_out = s.capped == 0u;
         if (s.ovf) {
             uint32_t *bad_flag = &cl.map_shared_rank(&s, 0)->ovf_bad;
             const uint32_t lane = lane_id();
@@ -858,7 +866,114 @@ __global__ void k_tail(const uint4 *vinfo, uint32_t n, uint32_t *tail) {
     }
 }
 
+// A single solve run as one instance of the batch kernel (DSSSP_MODE_TEAM): the
+// tables, queue, generator, error word and counters in a small region of the
+// graph handle, written here from the launch parameters.
+__global__ void k_team_setup(BatchArgs a, BGraphDev gd, BInstDev in, BGraphDev *gslot, BInstDev *islot) {
+    if (threadIdx.x == 0) {
+        *gslot = gd;
+        *islot = in;
+        *a.queue = 0u;
+        *a.gen = 0u;
+        *a.err = 0;
+    }
+    for (uint32_t i = threadIdx.x; i < (uint32_t)kBStats; i += blockDim.x) a.stats[i] = 0;
+}
+
+// Region layout: BGraphDev | BInstDev | queue, generator, error word | counters.
+constexpr size_t kTeamGraphOff = 0, kTeamInstOff = 128, kTeamWordsOff = 256, kTeamStatsOff = 384;
+
 }  // namespace
+
+size_t team_region_bytes() { return kTeamStatsOff + sizeof(long long) * kBStats; }
+
+cudaError_t team_solve_launch(dsssp_graph *g, const Split *sp, int32_t src, double delta, void *dist,
+                              int32_t *pred, int team_blocks, int64_t max_phases, cudaStream_t st) {
+    static_assert(sizeof(BGraphDev) <= kTeamInstOff - kTeamGraphOff, "team region layout");
+    static_assert(sizeof(BInstDev) <= kTeamWordsOff - kTeamInstOff, "team region layout");
+    char *r = static_cast<char *>(g->team_region);
+    const SolveArgs &w = g->args;
+    const size_t n = (size_t)g->n;
+    BatchArgs a{};
+    a.graphs = reinterpret_cast<const BGraphDev *>(r + kTeamGraphOff);
+    a.inst = reinterpret_cast<const BInstDev *>(r + kTeamInstOff);
+    a.n_inst = 1u;
+    a.queue = reinterpret_cast<uint32_t *>(r + kTeamWordsOff);
+    a.gen = a.queue + 1;
+    a.err = reinterpret_cast<int *>(a.queue + 2);
+    a.stats = reinterpret_cast<long long *>(r + kTeamStatsOff);
+    a.ws.packed = w.packed;              // the single-solve workspace serves as one team's slice
+    a.ws.nstamp = w.near_stamp;
+    a.ws.sstamp = w.s_stamp;
+    a.ws.fflag = w.b_stamp;
+    a.ws.F0 = w.F0;
+    a.ws.F1 = w.F1;
+    a.ws.S0 = w.S0;
+    a.ws.S1 = w.S1;
+    a.ws.X0 = w.OV0;
+    a.ws.X1 = w.OV1;
+    a.cap = n;
+    a.max_phases = max_phases;
+    BGraphDev gd{};
+    gd.vinfo = sp->vinfo;
+    gd.arcs = sp->arcs;
+    gd.perm = sp->perm;
+    gd.tail = nullptr;
+    gd.delta = delta;
+    gd.n = (uint32_t)g->n;
+    gd.m = (uint32_t)g->m;
+    BInstDev in{};
+    in.dist = dist;
+    in.pred = pred;
+    in.src = (uint32_t)src;
+    // stamps start from the generator's first value: no stamp of an earlier solve may match
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(w.near_stamp, 0, n * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.s_stamp, 0, n * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(w.b_stamp, 0, n * sizeof(uint32_t), st)) != cudaSuccess) return e;
+    k_team_setup<<<1, 32, 0, st>>>(a, gd, in, reinterpret_cast<BGraphDev *>(r + kTeamGraphOff),
+                                   reinterpret_cast<BInstDev *>(r + kTeamInstOff));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const void *kfn = g->dtype == DSSSP_F32 ? (const void *)k_batch<DSSSP_F32, false>
+                                            : (const void *)k_batch<DSSSP_I32, false>;
+    if (team_blocks > 8 && (e = cudaFuncSetAttribute(kfn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1)) !=
+                               cudaSuccess)
+        return e;
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute attr{};
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = (unsigned)team_blocks;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)team_blocks);
+    cfg.blockDim = dim3(kTeamThreads);
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    void *kargs[] = {&a};
+    return cudaLaunchKernelExC(&cfg, kfn, kargs);
+}
+
+int *team_err(dsssp_graph *g) { return reinterpret_cast<int *>(static_cast<char *>(g->team_region) + kTeamWordsOff + 8); }
+
+long long *team_stats(dsssp_graph *g) {
+    return reinterpret_cast<long long *>(static_cast<char *>(g->team_region) + kTeamStatsOff);
+}
+
+void team_stats_to_solve(const long long *st, dsssp_stats *out) {
+    out->buckets = st[BS_BUCKETS];
+    out->light_phases = st[BS_LIGHT];
+    out->heavy_phases = st[BS_HEAVY];
+    out->rebin_phases = st[BS_SELECT];
+    out->vertices_light = st[BS_VLIGHT];
+    out->vertices_heavy = st[BS_VHEAVY];
+    out->arcs_light = st[BS_ALIGHT];
+    out->arcs_heavy = st[BS_AHEAVY];
+    out->far_scanned = st[BS_FARSCAN];
+    out->improvements = st[BS_IMPROVE];
+    out->ns_total = st[BS_NS];
+}
+
 }  // namespace dsssp
 
 using namespace dsssp;

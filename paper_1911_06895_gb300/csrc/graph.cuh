@@ -40,6 +40,17 @@ dsssp_status cuda_status(cudaError_t e);
 // unpinned split evicted; UNSUPPORTED when all are pinned).
 dsssp_status ensure_split(dsssp_graph *g, double delta, cudaStream_t st, Split **out);
 
+// A single solve as one instance of the batch kernel on one thread-block cluster
+// of team_blocks blocks (DSSSP_MODE_TEAM), on the handle's workspace and region
+// (batch.cu). team_err / team_stats point into the region.
+size_t team_region_bytes();
+cudaError_t team_solve_launch(dsssp_graph *g, const Split *sp, int32_t src, double delta, void *dist,
+                              int32_t *pred, int team_blocks, int64_t max_phases, cudaStream_t st);
+int *team_err(dsssp_graph *g);
+long long *team_stats(dsssp_graph *g);
+void team_stats_to_solve(const long long *st, dsssp_stats *out);
+constexpr int kTeamStatsCount = 16;
+
 #define DSSSP_TRY(expr)                                      \
     do {                                                     \
         cudaError_t _e = (expr);                             \
@@ -67,6 +78,7 @@ struct dsssp_graph {
     dsssp::SolveArgs args{};
     dsssp::Ctl *ctl = nullptr;           // device
     dsssp::NaCtl *nactl = nullptr;       // device: control words of DSSSP_MODE_DENSE solves
+    void *team_region = nullptr;         // device: tables and counters of DSSSP_MODE_TEAM solves
     dsssp::Ctl *ctl_host = nullptr;      // pinned host mirror
     int32_t *sticky = nullptr;    // device: first error of asynchronous solves
     int occ_block = 0, occ_blocks_per_sm = 0;

@@ -60,8 +60,20 @@ struct Tried {
 
 // Device time of k dsssp_solve calls at one Delta (split built before timing);
 // solo_work as in dsssp_options (0: default).
+dsssp_status time_solves_opt(dsssp_graph *g, const int32_t *src, int32_t k, double delta, cudaStream_t st,
+                             double *ms, const dsssp_options &base);
+
 dsssp_status time_solves(dsssp_graph *g, const int32_t *src, int32_t k, double delta, cudaStream_t st, double *ms,
                          int32_t solo_work = 0) {
+    dsssp_options o;
+    dsssp_options_default(&o);
+    if (solo_work) o.solo_work = solo_work;
+    return time_solves_opt(g, src, k, delta, st, ms, o);
+}
+
+// Device time of k solves with the options `base` (asynchronous, one warm-up solve first).
+dsssp_status time_solves_opt(dsssp_graph *g, const int32_t *src, int32_t k, double delta, cudaStream_t st,
+                             double *ms, const dsssp_options &base) {
     dsssp_status rc = dsssp_prepare(g, delta, st);
     if (rc != DSSSP_OK) return rc;
     const size_t n = (size_t)g->n;
@@ -72,10 +84,8 @@ dsssp_status time_solves(dsssp_graph *g, const int32_t *src, int32_t k, double d
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    dsssp_options o;
-    dsssp_options_default(&o);
-    o.flags = DSSSP_FLAG_ASYNC;
-    if (solo_work) o.solo_work = solo_work;
+    dsssp_options o = base;
+    o.flags |= DSSSP_FLAG_ASYNC;
     rc = dsssp_solve(g, src[0], delta, dist, pred, &o, nullptr, st);      // warm-up
     if (rc == DSSSP_OK) rc = dsssp_graph_sync(g, st);
     if (rc == DSSSP_OK && cudaEventRecord(e0, st) != cudaSuccess) rc = DSSSP_ERR_CUDA;
@@ -297,6 +307,52 @@ extern "C" dsssp_status dsssp_tune_solo_work(dsssp_graph *g, const int32_t *samp
         }
     }
     *solo_work_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return DSSSP_OK;
+}
+
+extern "C" dsssp_status dsssp_tune_schedule(dsssp_graph *g, const int32_t *sample_src, int32_t k, double delta,
+                                            dsssp_options *opt_out, double *ms_out, void *stream) {
+    if (!g || !sample_src || k < 1 || !opt_out || !(delta > 0.0)) return DSSSP_ERR_INVALID_ARG;
+    for (int32_t j = 0; j < k; ++j)
+        if (sample_src[j] < 0 || (int64_t)sample_src[j] >= g->n) return DSSSP_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    double best_ms = std::numeric_limits<double>::infinity();
+    dsssp_options best;
+    dsssp_options_default(&best);
+    // the persistent grid-wide scheme at each solo threshold
+    for (int32_t sw : {-1, 512, 2048, 8192, 32768}) {
+        dsssp_options o;
+        dsssp_options_default(&o);
+        o.solo_work = sw;
+        double ms = 0.0;
+        dsssp_status rc = time_solves_opt(g, sample_src, k, delta, st, &ms, o);
+        if (rc != DSSSP_OK) return rc;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = o;
+        }
+    }
+    // one thread-block cluster (a batch team) per solve
+    for (int32_t tb : {8, 16}) {
+        dsssp_options o;
+        dsssp_options_default(&o);
+        o.mode = DSSSP_MODE_TEAM;
+        o.team_blocks = tb;
+        double ms = 0.0;
+        dsssp_status rc = time_solves_opt(g, sample_src, k, delta, st, &ms, o);
+        if (rc == DSSSP_ERR_UNSUPPORTED || rc == DSSSP_ERR_CUDA) {   // this cluster size cannot run here
+            cudaGetLastError();
+            continue;
+        }
+        if (rc != DSSSP_OK) return rc;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = o;
+        }
+    }
+    *opt_out = best;
     if (ms_out) *ms_out = best_ms;
     return DSSSP_OK;
 }

@@ -43,6 +43,7 @@ DSSSP_F32 = 1
 DSSSP_MODE_PERSISTENT = 0
 DSSSP_MODE_STEPPED = 1
 DSSSP_MODE_DENSE = 2
+DSSSP_MODE_TEAM = 3
 DSSSP_FLAG_ASYNC = 0x1
 DSSSP_FLAG_NO_FUSE = 0x2
 DSSSP_HOOK_NONE = 0
@@ -127,6 +128,9 @@ dsssp_autotune = _fn("dsssp_autotune", ctypes.c_int,
                      [_vp, _i32, _vp, _i32, ctypes.POINTER(dsssp_tune_options), _vp, _vp, _vp])
 dsssp_tune_solo_work = _fn("dsssp_tune_solo_work", ctypes.c_int,
                            [_vp, _vp, _i32, ctypes.c_double, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double), _vp])
+dsssp_tune_schedule = _fn("dsssp_tune_schedule", ctypes.c_int,
+                          [_vp, _vp, _i32, ctypes.c_double, ctypes.POINTER(dsssp_options),
+                           ctypes.POINTER(ctypes.c_double), _vp])
 dsssp_tune_team_blocks = _fn("dsssp_tune_team_blocks", ctypes.c_int,
                              [_vp, _i32, _vp, _i32, _vp, _vp, _vp, _vp, ctypes.POINTER(_i32),
                               ctypes.POINTER(ctypes.c_double), _vp])
@@ -135,7 +139,7 @@ EXPORTED = ["dsssp_status_string", "dsssp_options_default", "dsssp_graph_create"
             "dsssp_graph_info", "dsssp_prepare", "dsssp_solve", "dsssp_graph_sync", "dsssp_solve_noalloc",
             "dsssp_batch_create", "dsssp_batch_run", "dsssp_batch_sync", "dsssp_batch_destroy",
             "dsssp_solve_batched", "dsssp_backward", "dsssp_autotune", "dsssp_tune_team_blocks",
-            "dsssp_tune_solo_work"]
+            "dsssp_tune_solo_work", "dsssp_tune_schedule"]
 
 NOALLOC_MAX_VERTICES = 1 << 17
 
@@ -427,3 +431,15 @@ def tune_solo_work(graph, sample_sources, delta, stream=None):
                                float(delta), ctypes.byref(sw), ctypes.byref(ms), _stream_ptr(stream)),
           "dsssp_tune_solo_work")
     return int(sw.value), float(ms.value)
+
+
+def tune_schedule(graph, sample_sources, delta, stream=None):
+    """Fastest scheme of single solves for one graph at one Delta (persistent with a solo
+    threshold, or one thread-block cluster per solve); returns (options, ms)."""
+    k = len(sample_sources)
+    o = dsssp_options()
+    ms = ctypes.c_double(0.0)
+    check(dsssp_tune_schedule(graph.handle, (ctypes.c_int32 * k)(*[int(s) for s in sample_sources]), k,
+                              float(delta), ctypes.byref(o), ctypes.byref(ms), _stream_ptr(stream)),
+          "dsssp_tune_schedule")
+    return o, float(ms.value)

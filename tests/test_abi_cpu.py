@@ -30,7 +30,7 @@ def test_library_exports_every_declared_entry_point():
 
 def test_status_strings_and_defaults():
     import paper_1911_06895_gb300 as ds
-    for s in range(12):
+    for s in range(13):
         assert ds.dsssp_status_string(s) != b"unknown status"
     assert ds.dsssp_status_string(999) == b"unknown status"
     o = ds.make_options()

@@ -51,8 +51,9 @@ def assert_same(g, src, d, p, d_ref=None, p_ref=None, what=""):
 
 
 # persistent, stepped, a small grid, heavy passes kept apart from the next bucket (DSSSP_FLAG_NO_FUSE),
-# and the full-vector form (DSSSP_MODE_DENSE)
-MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64), dict(flags=2), dict(mode=2)]
+# the full-vector form (DSSSP_MODE_DENSE), and one thread-block cluster per solve (DSSSP_MODE_TEAM)
+MODES = [dict(), dict(mode=1), dict(grid_size=3, block_size=64), dict(flags=2), dict(mode=2), dict(mode=3),
+         dict(mode=3, team_blocks=2)]
 
 
 # ------------------------------------------------------------------ hand-built cases
@@ -339,7 +340,7 @@ def test_bounded_wait_times_out_and_context_survives(ds):
 def test_phase_cap_not_converged(ds):
     g, srcs, deltas = W.rmat14_int(scale=11)
     h = ds.Graph(g.row_ptr, g.col, g.w)
-    for mode in (0, 1):
+    for mode in (0, 1, 3):
         with pytest.raises(ds.DsssError) as e:
             h.solve(srcs[0], deltas[0], options=ds.make_options(max_phases=3, mode=mode))
         assert e.value.status == ds.DSSSP_ERR_NOT_CONVERGED
@@ -384,5 +385,6 @@ def test_full_grid4096_all_deltas_exact(ds):
     h = ds.Graph(g.row_ptr, g.col, g.w)
     d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
     for delta in deltas:
-        d, p, _ = gpu_solve(ds, h, 0, delta)
-        assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta}")
+        for opt in (dict(), dict(mode=3)):
+            d, p, _ = gpu_solve(ds, h, 0, delta, **opt)
+            assert_same(g, 0, d, p, d_ref, p_ref, f"delta {delta} {opt}")

@@ -91,3 +91,24 @@ def test_tune_solo_work(ds):
     r = h.solve(sources[2], 0.05, options=ds.make_options(solo_work=sw))
     d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, sources[2])
     assert np.array_equal(r.dist.cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
+
+
+def test_tune_schedule_picks_a_scheme_and_it_is_exact(ds):
+    """The schedule tuner times the persistent scheme at each solo threshold and the one-cluster
+    scheme at 8 and 16 blocks; the options it returns solve exactly. On a high-diameter grid the
+    one-cluster scheme is expected to win, on a small-world R-MAT the grid-wide one."""
+    g, srcs, _ = W.grid4096(side=400)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    o, ms = ds.tune_schedule(h, [0, 1], 100.0)
+    assert ms > 0 and o.mode in (ds.DSSSP_MODE_PERSISTENT, ds.DSSSP_MODE_TEAM)
+    assert o.mode == ds.DSSSP_MODE_TEAM
+    r = h.solve(0, 100.0, options=o)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, 0)
+    assert np.array_equal(r.dist.cpu().numpy(), d_ref) and np.array_equal(r.pred.cpu().numpy(), p_ref)
+    g, sources, _ = W.rmat22_unit(scale=16, n_sources=3)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    o, ms = ds.tune_schedule(h, sources[:2], 0.5)
+    r = h.solve(sources[2], 0.5, options=o)
+    d_ref, p_ref = oracle.dijkstra(g.row_ptr, g.col, g.w, sources[2])
+    assert np.array_equal(r.dist.cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
+    assert np.array_equal(r.pred.cpu().numpy(), p_ref)
