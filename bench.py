@@ -289,25 +289,30 @@ def main():
             split_ms[str(d)] = e0.elapsed_time(e1)
         dist = torch.empty(g.n, dtype=torch.float32, device="cuda")
         pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
-        # schedule: the solo threshold per Delta from the tuner (two sample sources, untimed)
-        solo = {}
+        # schedule per Delta from the tuner (two sample sources, untimed): the grid-wide persistent
+        # scheme with its solo threshold, or one thread-block cluster per solve
+        sched = {}
         for d in deltas:
-            solo[d] = ds.tune_solo_work(h, srcs[:2], d, stream=stream)[0] if args.mode == 0 else 2048
-        opts = {d: ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=args.mode, solo_work=solo[d]) for d in deltas}
+            if args.mode == 0:
+                o, _ = ds.tune_schedule(h, srcs[:2], d, stream=stream)
+                sched[d] = dict(mode=o.mode, solo_work=o.solo_work, team_blocks=o.team_blocks)
+            else:
+                sched[d] = dict(mode=args.mode, solo_work=2048, team_blocks=0)
+        opts = {d: ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, **sched[d]) for d in deltas}
 
         # arcs out of reached vertices per source (Delta does not change which vertices are reached)
         deg = torch.from_numpy(np.diff(g.row_ptr)).to("cuda")
         m_reached = {}
         for s in srcs:
             h.solve(s, deltas[0], dist=dist, pred=pred, stream=stream,
-                    options=ds.make_options(mode=args.mode, solo_work=solo[deltas[0]]))
+                    options=ds.make_options(**sched[deltas[0]]))
             m_reached[s] = int(deg[torch.isfinite(dist)].sum().item())
 
         # per-solve statistics (one untimed pass) -> algorithmic bytes
         stats = {}
         for d in deltas:
             stats[d] = [h.solve(s, d, dist=dist, pred=pred, stream=stream, stats=True,
-                                options=ds.make_options(mode=args.mode, solo_work=solo[d])).stats for s in srcs]
+                                options=ds.make_options(**sched[d])).stats for s in srcs]
 
         def one_step(record):
             for d in deltas:
@@ -388,7 +393,7 @@ def main():
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, solo)
+        e2e = run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, sched)
 
     extras = {}
     if world == 1 and not args.no_extras:
@@ -419,7 +424,7 @@ def main():
                        "n": g.n, "m": g.m, "sources": len(srcs), "deltas": deltas, "solves_per_step": solves,
                        "mode": "persistent" if args.mode == 0 else "stepped",
                        "l2": "inputs larger than L2 (arcs %.0f MB per Delta)" % (g.m * 8 / 1e6),
-                       "split_ms": split_ms, "solo_work": {str(d): solo[d] for d in deltas},
+                       "split_ms": split_ms, "schedule": {str(d): sched[d] for d in deltas},
                        "mean_reached_arcs": sum(m_reached.values()) / len(srcs), "per_delta": per_delta,
                        "parallelism": f"replicas{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -431,7 +436,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
-            "gpu_launches": 4 * solves * args.steps,
+            "gpu_launches": sum((3 if sched[d]["mode"] == 3 else 4) * len(srcs) for d in deltas) * args.steps,
         }
         line.update(extras)
         if batched_same is not None:
@@ -659,30 +664,37 @@ def run_other_workloads(ds, torch):
     """The other single-source workloads: the 4096 x 4096 grid (int32 U{1..1000}, 5 % of arcs
     dropped, corner source, Delta in {100, 1000, 10000}: the high-diameter, phase-bound case)
     and the scale-14 R-MAT (int32 U{1..255}, Delta 32, highest out-degree source). Per Delta:
-    device time per solve (CUDA events, median of several), GTEPS, phases and the algorithmic
-    bandwidth of the solve against the measured HBM copy peak."""
+    the scheme chosen by the schedule tuner (untimed, one sample source), its device time per
+    solve (CUDA events, median of several), GTEPS, phases and the algorithmic bandwidth of the
+    solve against the measured HBM copy peak; and the grid-wide persistent scheme beside it."""
     import graphgen.workloads as W
     peak, _ = measured_peak_gbs()
     out = {}
     for name, (g, srcs, deltas), reps in (("grid4096_int", W.grid4096(), 3), ("rmat14_int", W.rmat14_int(), 20)):
         h = ds.Graph(g.row_ptr, g.col, g.w)
-        tdt = torch.int32
-        dist = torch.empty(g.n, dtype=tdt, device="cuda")
+        dist = torch.empty(g.n, dtype=torch.int32, device="cuda")
         pred = torch.empty(g.n, dtype=torch.int32, device="cuda")
         s = srcs[0]
         per = {}
         for d in deltas:
             h.prepare(d)
-            st = h.solve(s, d, dist=dist, pred=pred, stats=True).stats
-            o = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC)
-            ms = _events_ms(torch, lambda: h.solve(s, d, dist=dist, pred=pred, options=o), reps)
-            h.sync()
-            b = algorithmic_bytes(st, g.n)
-            per[str(d)] = {"ms_per_solve": ms, "gteps": g.m / (ms * 1e-3) / 1e9,
-                           "phases": st["light_phases"] + st["heavy_phases"] + st["rebin_phases"],
-                           "buckets": st["buckets"], "arcs_relaxed": st["arcs_light"] + st["arcs_heavy"],
-                           "roofline": {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": peak,
-                                        "unit": "GB/s", "frac": b / (ms * 1e-3) / 1e9 / peak}}
+            tuned, _ = ds.tune_schedule(h, [s], d)
+            row = {}
+            for label, o in (("tuned", tuned), ("persistent", ds.make_options())):
+                st = h.solve(s, d, dist=dist, pred=pred, stats=True, options=o).stats
+                oa = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, mode=o.mode, solo_work=o.solo_work,
+                                     team_blocks=o.team_blocks)
+                ms = _events_ms(torch, lambda: h.solve(s, d, dist=dist, pred=pred, options=oa), reps)
+                h.sync()
+                b = algorithmic_bytes(st, g.n)
+                row[label] = {"mode": ["persistent", "stepped", "dense", "team"][o.mode],
+                              "solo_work": o.solo_work, "team_blocks": st["grid_size"] if o.mode == 3 else 0,
+                              "ms_per_solve": ms, "gteps": g.m / (ms * 1e-3) / 1e9,
+                              "phases": st["light_phases"] + st["heavy_phases"] + st["rebin_phases"],
+                              "buckets": st["buckets"], "arcs_relaxed": st["arcs_light"] + st["arcs_heavy"],
+                              "roofline": {"bound": "hbm", "achieved": b / (ms * 1e-3) / 1e9, "peak": peak,
+                                           "unit": "GB/s", "frac": b / (ms * 1e-3) / 1e9 / peak}}
+            per[str(d)] = row
         h.close()
         out[name] = {"n": g.n, "m": g.m, "source": s, "per_delta": per}
     return out
@@ -748,7 +760,7 @@ def profile_driver(args):
     torch.cuda.synchronize()
 
 
-def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, solo):
+def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, sched):
     """Public-API end to end: host CSR -> graph -> 256 solves -> results in pinned host memory.
 
     Each solve writes one of NB device buffers; its result goes back to pinned host memory on a copy
@@ -773,7 +785,7 @@ def run_e2e(ds, torch, g, srcs, deltas, world, dist_pg, args, solo):
         copied = [None] * NB
         k = 0
         for d in deltas:
-            opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, solo_work=solo[d])
+            opt = ds.make_options(flags=ds.DSSSP_FLAG_ASYNC, **sched[d])
             for s in srcs:
                 b = k % NB
                 if copied[b] is not None:
