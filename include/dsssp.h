@@ -303,8 +303,8 @@ dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream);
 
 /* Wait for `stream`, then return (and clear) the first device-side status of the runs and
  * backward passes since the last sync (NOT_CONVERGED when an instance hit the phase cap,
- * OVERFLOW when a path sum of an instance overflowed -- that instance's outputs are then
- * not written -- and DEGENERATE from dsssp_backward). stats: NULL or a HOST array of n_inst records, filled
+ * OVERFLOW when a path sum of an instance overflowed -- in both cases that instance's outputs
+ * are not written -- and DEGENERATE from dsssp_backward). stats: NULL or a HOST array of n_inst records, filled
  * from the last run, in the caller's instance order. */
 dsssp_status dsssp_batch_sync(dsssp_batch *b, dsssp_batch_stats *stats, void *stream);
 
