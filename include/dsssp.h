@@ -119,7 +119,9 @@ typedef struct {
                                thread-block cluster of 1, 2, 4, 8 or 16; 16 is a non-portable
                                cluster size, UNSUPPORTED where it cannot be co-scheduled);
                                0 = automatic (batches: 1-8, more blocks per instance when
-                               instances are few; team solves: 16, else 8)                        */
+                               instances are few; team solves: 16, else 8). Batches only: -1 =
+                               the instances one after another, each by the grid-wide persistent
+                               solver (no tape; a run then cannot be captured into a CUDA graph) */
     int32_t  reserved[4];
 } dsssp_options;
 
@@ -298,7 +300,9 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
 /* Enqueue one run of every instance on `stream`: a single launch of the plan's CUDA graph
  * (queue reset + the persistent kernel). While `stream` is being captured into a caller's CUDA
  * graph, the two operations are enqueued directly and become nodes of that graph. Allocates
- * nothing and does not wait. Errors: INVALID_ARG, CUDA. */
+ * nothing and does not wait. A plan with team_blocks = -1 enqueues one dsssp_solve per instance
+ * instead (the first run may allocate the graphs' workspaces; UNSUPPORTED while capturing).
+ * Errors: INVALID_ARG, CUDA, UNSUPPORTED. */
 dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream);
 
 /* Wait for `stream`, then return (and clear) the first device-side status of the runs and
@@ -389,7 +393,8 @@ dsssp_status dsssp_tune_schedule(dsssp_graph *g, const int32_t *sample_src, int3
                                  dsssp_options *opt_out, double *ms_out, void *stream);
 
 /* Choose the team size of a batch (dsssp_options.team_blocks: blocks per instance, 1, 2, 4, 8
- * or 16; sizes that cannot be co-scheduled are skipped) by timing the whole batch at each size: builds the plan the arguments describe (as
+ * or 16, and -1 -- one instance after another on the whole GPU -- when every instance is on one
+ * graph; sizes that cannot be co-scheduled are skipped) by timing the whole batch at each size: builds the plan the arguments describe (as
  * dsssp_batch_create, outputs written) once per size, runs it twice and keeps the fastest
  * second run. team_blocks_out receives the size; ms_out (may be NULL) its device time.
  * Waits for its work. Errors: those of dsssp_batch_create / run / sync. */

@@ -1014,11 +1014,19 @@ struct dsssp_batch {
     const void *kfn = nullptr;              // the forward kernel of this plan
     void *h_ptrs = nullptr;                 // pinned staging for backward pointer tables
     long long max_phases = 0;
+    // team_blocks = -1: the instances one after another, each by the grid-wide persistent solver
+    bool seq = false;
+    std::vector<int32_t> seq_graph, seq_src;
+    std::vector<void *> seq_dist;
+    std::vector<int32_t *> seq_pred;
+    std::vector<double> seq_delta;          // per graph
+    Ctl *h_ctl = nullptr;                   // pinned: every instance's control block after its solve
 };
 
 namespace {
 
 void release(dsssp_batch *b) {
+    if (b->h_ctl) cudaFreeHost(b->h_ctl);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->mem);
@@ -1088,6 +1096,28 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
         if (rc != DSSSP_OK) return fail(rc);
         sp->pins++;
         b->splits[i] = sp;
+    }
+    if (o.team_blocks == -1) {
+        // one instance after another on the whole GPU (the single-solve kernel): for workloads
+        // whose instances each fill the GPU and whose working sets fit L2 only one at a time
+        if (tape) return fail(DSSSP_ERR_UNSUPPORTED);
+        b->seq = true;
+        b->csize = 0;
+        b->seq_delta.assign(delta, delta + n_graphs);
+        for (int32_t k = 0; k < n_inst; ++k) {
+            b->seq_graph.push_back(src_graph ? src_graph[k] : 0);
+            b->seq_src.push_back(src[k]);
+            b->seq_dist.push_back(dist[k]);
+            b->seq_pred.push_back(pred ? pred[k] : nullptr);
+        }
+        cudaError_t ce = cudaMallocHost(&b->h_ctl, sizeof(Ctl) * (size_t)n_inst);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            return fail(cuda_status(ce));
+        }
+        *out = b;
+        return DSSSP_OK;
     }
     // team size (blocks per instance): a cluster when instances are fewer than the blocks
     int bps = 0, sms = 0;
@@ -1339,6 +1369,23 @@ dsssp_status dsssp_batch_run(dsssp_batch *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     DSSSP_TRY(cudaStreamIsCapturing(st, &cap));
+    if (b->seq) {
+        if (cap != cudaStreamCaptureStatusNone) return DSSSP_ERR_UNSUPPORTED;
+        dsssp_options o;
+        dsssp_options_default(&o);
+        o.flags = DSSSP_FLAG_ASYNC;
+        o.max_phases = b->max_phases;
+        for (int32_t k = 0; k < b->n_inst; ++k) {
+            dsssp_graph *g = b->graphs[b->seq_graph[k]];
+            dsssp_status rc = dsssp_solve(g, b->seq_src[k], b->seq_delta[b->seq_graph[k]], b->seq_dist[k],
+                                          b->seq_pred[k], &o, nullptr, stream);
+            if (rc != DSSSP_OK) return rc;
+            // the solve's counters, for dsssp_batch_sync
+            DSSSP_TRY(cudaMemcpyAsync(b->h_ctl + k, g->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        }
+        b->ran = true;
+        return DSSSP_OK;
+    }
     if (cap == cudaStreamCaptureStatusActive) {
         // the caller is recording a graph of its own: the same two operations go in as its nodes
         DSSSP_TRY(cudaMemsetAsync(b->d_queue, 0, sizeof(uint32_t), st));
@@ -1366,6 +1413,33 @@ dsssp_status dsssp_batch_sync(dsssp_batch *b, dsssp_batch_stats *stats, void *st
     if (!b) return DSSSP_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     cudaStream_t st = (cudaStream_t)stream;
+    if (b->seq) {
+        dsssp_status first = DSSSP_OK;
+        for (dsssp_graph *g : b->graphs) {            // waits for the stream; each graph's first error
+            const dsssp_status rc = dsssp_graph_sync(g, stream);
+            if (first == DSSSP_OK) first = rc;
+        }
+        if (stats) {
+            for (int32_t k = 0; k < b->n_inst; ++k) {
+                const long long *x = b->h_ctl[k].ss.st;
+                dsssp_batch_stats &o = stats[k];
+                std::memset(&o, 0, sizeof o);
+                o.buckets = x[ST_BUCKETS];
+                o.light_phases = x[ST_LIGHT];
+                o.heavy_phases = x[ST_HEAVY];
+                o.select_phases = x[ST_REBIN];
+                o.arcs_light = x[ST_ALIGHT];
+                o.arcs_heavy = x[ST_AHEAVY];
+                o.improvements = x[ST_IMPROVE];
+                o.far_scanned = x[ST_FARSCAN];
+                o.ns = x[ST_NSTOTAL];
+                o.team = -1;
+                o.vertices_light = x[ST_VLIGHT];
+                o.vertices_heavy = x[ST_VHEAVY];
+            }
+        }
+        return first;
+    }
     int err = 0;
     std::vector<long long> hs;
     DSSSP_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));

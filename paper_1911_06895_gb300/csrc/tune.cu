@@ -255,7 +255,9 @@ extern "C" dsssp_status dsssp_tune_team_blocks(dsssp_graph *const *graphs, int32
     double best_ms = std::numeric_limits<double>::infinity();
     int32_t best = 0;
     dsssp_status rc = DSSSP_OK;
-    for (int32_t tb : {1, 2, 4, 8, 16}) {
+    for (int32_t tb : {1, 2, 4, 8, 16, -1}) {
+        // -1: one instance after another on the whole GPU (tried for a batch on one graph)
+        if (tb == -1 && n_graphs != 1) continue;
         dsssp_options o;
         dsssp_options_default(&o);
         o.team_blocks = tb;

@@ -6,6 +6,7 @@ compared with the oracle's float64 subtree sums over the same tree (relative
 error <= 1e-5 per arc) and, independently, with central differences of the
 loss taken through the forward solve itself.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -496,3 +497,31 @@ def test_full_rmat20_lognormal_central_differences(ds):
                                f"fd {fd[ok][bad[:5]]}")
         if name == "tree arcs":
             assert np.count_nonzero(fd[ok]) >= need
+
+
+def test_batch_one_after_another_on_the_whole_gpu(ds):
+    """team_blocks = -1: the plan runs its instances one after another with the grid-wide solver;
+    same bits, counters filled, no tape, and a run refuses a stream being captured."""
+    g, sources, _ = W.rmat22_unit(scale=15, n_sources=6)
+    h = ds.Graph(g.row_ptr, g.col, g.w)
+    refd, refp, _ = oracle.dijkstra_many(g.row_ptr, g.col, g.w, sources)
+    b = batch(ds, h, [0.1], sources, team_blocks=-1)
+    for rep in range(2):
+        b.run()
+        st = b.sync(stats=True)
+        ds_, ps_ = fetch(b)
+        for k, s in enumerate(sources):
+            same(ds_[k], ps_[k], refd[k], refp[k], f"rep {rep} src {s}")
+    assert all(x["team"] == -1 and x["arcs_light"] + x["arcs_heavy"] > 0 and x["buckets"] >= 1 for x in st)
+    s_ = torch.cuda.Stream()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s_):
+        cg.capture_begin()
+        b.dist[0].fill_(0)
+        rc = ds.dsssp_batch_run(b.handle, ctypes.c_void_p(s_.cuda_stream))
+        cg.capture_end()
+    assert rc == ds.DSSSP_ERR_UNSUPPORTED
+    b.close()
+    with pytest.raises(ds.DsssError) as e:
+        ds.Batch(h, [0.1], sources, tape=True, options=ds.make_options(team_blocks=-1))
+    assert e.value.status == ds.DSSSP_ERR_UNSUPPORTED
