@@ -97,6 +97,8 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     const size_t o_sh = bytes;     bytes += up(n * 4 * kSlots);
     const size_t o_ov0 = bytes;    bytes += up(n * 4);
     const size_t o_ov1 = bytes;    bytes += up(n * 4);
+    const uint32_t dcap = solve_dir_entries((uint32_t)g->n, (uint32_t)g->m);
+    const size_t o_dir = bytes;    bytes += up((size_t)dcap * kDirLists * 8);
     const size_t o_ctl = bytes;    bytes += up(sizeof(Ctl));
     const size_t o_nactl = bytes;  bytes += up(sizeof(NaCtl));
     const size_t o_team = bytes;   bytes += up(team_region_bytes());
@@ -121,6 +123,8 @@ dsssp_status ensure_workspace(dsssp_graph *g) {
     a.SH = (uint32_t *)(base + o_sh);
     a.OV0 = (uint32_t *)(base + o_ov0);
     a.OV1 = (uint32_t *)(base + o_ov1);
+    a.dir = (uint2 *)(base + o_dir);
+    a.dcap = dcap;
     a.ctl = (Ctl *)(base + o_ctl);
     g->ctl = a.ctl;
     g->nactl = (NaCtl *)(base + o_nactl);

@@ -79,7 +79,11 @@ struct BInstDev {
     uint32_t graph, src, orig, pad;
 };
 
-// Per-team working memory: array x of team t starts at x + t * cap.
+// Per-team working memory: array x of team t starts at x + t * cap (times the
+// array's stride for packed and the two stamps). In a batch plan a vertex's
+// packed word and its two stamps share one 16-byte record (strides 2 and 4), so
+// a relaxation and the bookkeeping of the improvement it makes touch one 32-byte
+// sector; the single-solve workspace keeps them in separate arrays (strides 1).
 struct TeamWS {
     unsigned long long *packed;
     uint32_t *nstamp;          // phase stamp of the last push into the next frontier
@@ -87,6 +91,8 @@ struct TeamWS {
     uint32_t *fflag;           // instance stamp while the vertex has a far-list entry
     uint2 *F0, *F1, *S0, *S1;  // (vertex, exclusive arc offset)
     uint32_t *X0, *X1;         // far lists
+    uint32_t pst;              // packed stride in 64-bit words
+    uint32_t sts;              // nstamp / sstamp stride in 32-bit words
 };
 
 struct BatchArgs {
@@ -118,6 +124,7 @@ struct Ph {
     const uint32_t *xin;            // SELECT: the far list read
     uint32_t count, arcs;           // its entries and arcs
     uint32_t *nstamp, *sstamp, *fflag;
+    uint32_t sts;                   // stride of nstamp / sstamp
     uint32_t *far_min, *next_min;   // team reductions
     uint32_t *ovf;                  // team flag: a relaxation met a sum the weight type cannot hold
     unsigned long long *improve, *a_light, *a_heavy;
@@ -163,6 +170,8 @@ struct Team {
     const uint32_t *perm;      // split position -> input arc index (tape)
     unsigned long long *packed;
     uint32_t n, m;
+    uint32_t pst;              // packed stride
+    __device__ __forceinline__ unsigned long long *pk(uint32_t v) const { return packed + (size_t)v * pst; }
 };
 
 struct TPush {
@@ -193,14 +202,14 @@ template <int DT>
 __device__ __forceinline__ void on_improved(const Team &t, const Ph &ph, uint32_t v, uint32_t ck, TPush &p,
                                             uint32_t &far_min) {
     if (ck < ph.T) {
-        const uint32_t prev = atomicExch(ph.nstamp + v, ph.pstamp);
+        const uint32_t prev = atomicExch(ph.nstamp + (size_t)v * ph.sts, ph.pstamp);
         const uint4 vi = t.vinfo[v];
-        const uint32_t ss = __ldcg(ph.sstamp + v);
+        const uint32_t ss = __ldcg(ph.sstamp + (size_t)v * ph.sts);
         if (prev == ph.pstamp) return;
         p.fdeg = vi.y - vi.x;
         p.f = p.fdeg != 0u;
         if (ss != ph.sst) {
-            ph.sstamp[v] = ph.sst;
+            ph.sstamp[(size_t)v * ph.sts] = ph.sst;
             p.sdeg = vi.z - vi.y;
             p.s = p.sdeg != 0u;
         }
@@ -310,7 +319,7 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
                 const uint2 en = __ldcg(list + idx);
                 wv = en.x < t.n ? en.x : 0u;
                 woff = en.y;
-                wkey = (uint32_t)(__ldcg(t.packed + wv) >> 32);
+                wkey = (uint32_t)(__ldcg(t.pk(wv)) >> 32);
                 const uint4 vi = t.vinfo[wv];
                 wbeg = LIGHT ? vi.x : vi.y;
             } else {
@@ -374,7 +383,7 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
             for (int k = 0; k < kTIlp; ++k) {
                 ck[k] = ok[k] ? key_add<DT>(okey[k], arc[k].y) : inf_key<DT>();
                 ovf |= ok[k] && ck[k] >= inf_key<DT>();
-                cur[k] = ck[k] < inf_key<DT>() ? __ldcg(t.packed + arc[k].x) : 0ull;
+                cur[k] = ck[k] < inf_key<DT>() ? __ldcg(t.pk(arc[k].x)) : 0ull;
             }
             // with a tape the low word is the arc's input index, read only for a
             // request that can win or tie on the key
@@ -389,7 +398,7 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
             unsigned long long old[kTIlp];
             #pragma unroll
             for (int k = 0; k < kTIlp; ++k)
-                old[k] = (ck[k] < inf_key<DT>() && cand[k] < cur[k]) ? atomicMin(t.packed + arc[k].x, cand[k]) : 0ull;
+                old[k] = (ck[k] < inf_key<DT>() && cand[k] < cur[k]) ? atomicMin(t.pk(arc[k].x), cand[k]) : 0ull;
             #pragma unroll
             for (int k = 0; k < kTIlp; ++k) {
                 const bool imp = cand[k] < old[k] && (uint32_t)(old[k] >> 32) > ck[k];   // strict decrease
@@ -430,7 +439,7 @@ __device__ void team_select(const Team &t, const Ph &ph, TStage &ws, uint32_t &n
         TPush p{};
         uint32_t v = NONE;
         if (idx < count && (v = __ldcg(xin + idx)) < t.n) {          // written by other blocks of the team
-            const uint32_t k = (uint32_t)(__ldcg(t.packed + v) >> 32);
+            const uint32_t k = (uint32_t)(__ldcg(t.pk(v)) >> 32);
             if (k < ph.T_lo) {
                 ph.fflag[v] = 0u;                    // its bucket was processed
             } else if (k < ph.T) {
@@ -438,7 +447,7 @@ __device__ void team_select(const Team &t, const Ph &ph, TStage &ws, uint32_t &n
                 const uint4 vi = t.vinfo[v];
                 p.fdeg = vi.y - vi.x;
                 p.f = p.fdeg != 0u;
-                ph.sstamp[v] = ph.sst;
+                ph.sstamp[(size_t)v * ph.sts] = ph.sst;
                 p.sdeg = vi.z - vi.y;
                 p.s = p.sdeg != 0u;
             } else {
@@ -545,8 +554,9 @@ __device__ __noinline__ void build_view(Ph &ph, TeamShared *L, const BatchArgs &
     ph.xin = (xcur ? a.ws.X1 : a.ws.X0) + off;
     ph.count = (uint32_t)(c >> 32);
     ph.arcs = (uint32_t)c;
-    ph.nstamp = a.ws.nstamp + off;
-    ph.sstamp = a.ws.sstamp + off;
+    ph.nstamp = a.ws.nstamp + off * a.ws.sts;
+    ph.sstamp = a.ws.sstamp + off * a.ws.sts;
+    ph.sts = a.ws.sts;
     ph.fflag = a.ws.fflag + off;
     ph.far_min = &L->far_min;
     ph.next_min = &L->next_min;
@@ -576,11 +586,12 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
     const uint32_t team = blockIdx.x / csize;
     const size_t off = (size_t)team * a.cap;
     Team t;
-    t.packed = a.ws.packed + off;
+    t.packed = a.ws.packed + off * a.ws.pst;
+    t.pst = a.ws.pst;
     if (leader && tid == 0) {
         s.gen = a.gen[team];
-        s.nstamp = a.ws.nstamp + off;
-        s.sstamp = a.ws.sstamp + off;
+        s.nstamp = a.ws.nstamp + off * a.ws.sts;
+        s.sstamp = a.ws.sstamp + off * a.ws.sts;
         s.fflag = a.ws.fflag + off;
     }
     for (;;) {
@@ -606,15 +617,15 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
         // stamps restart from 1 before the leader's generator could wrap
         if (s.gen_seen > 0xF0000000u) {
             for (size_t v = team_thread(); v < a.cap; v += team_threads()) {
-                a.ws.nstamp[off + v] = 0u;
-                a.ws.sstamp[off + v] = 0u;
+                a.ws.nstamp[(off + v) * a.ws.sts] = 0u;
+                a.ws.sstamp[(off + v) * a.ws.sts] = 0u;
                 a.ws.fflag[off + v] = 0u;
             }
             cl.sync();
             if (leader && tid == 0) s.gen = 1u;
         }
         const unsigned long long init = ((unsigned long long)inf_key<DT>() << 32) | NONE;
-        for (uint32_t v = team_thread(); v < t.n; v += team_threads()) t.packed[v] = init;
+        for (uint32_t v = team_thread(); v < t.n; v += team_threads()) *t.pk(v) = init;
         cl.sync();
         if (leader && tid == 0) {
             s.t0 = wu::globaltimer();
@@ -635,7 +646,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             s.T_lo = 0u;
             s.T = bucket_floor_key(1, DT, s.G.delta);    // bucket 0 holds the source
             const uint32_t src = s.I.src;
-            t.packed[src] = TAPE ? (unsigned long long)NONE : (unsigned long long)src;   // key 0
+            *t.pk(src) = TAPE ? (unsigned long long)NONE : (unsigned long long)src;   // key 0
             const uint4 vi = s.G.vinfo[src];
             if (vi.y > vi.x) {
                 a.ws.F0[off] = make_uint2(src, 0u);
@@ -645,7 +656,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
                 a.ws.S0[off] = make_uint2(src, 0u);
                 s.ctrS[0] = (1ull << 32) | (vi.z - vi.y);
             }
-            s.sstamp[src] = s.sst;
+            s.sstamp[(size_t)src * a.ws.sts] = s.sst;
             s.mode = (s.ctrF[0] >> 32) ? T_LIGHT : ((s.ctrS[0] >> 32) ? T_HEAVY : T_DONE);
             if (s.mode == T_HEAVY) s.sst = ++s.gen;
         }
@@ -697,7 +708,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             uint32_t *bad_flag = &cl.map_shared_rank(&s, 0)->ovf_bad;
             const uint32_t lane = lane_id();
             for (uint32_t v = team_warp(); v < t.n; v += team_warps()) {
-                const uint32_t k = (uint32_t)(__ldcg(t.packed + v) >> 32);
+                const uint32_t k = (uint32_t)(__ldcg(t.pk(v)) >> 32);
                 if (k >= inf_key<DT>()) continue;
                 const uint4 vi = t.vinfo[v];
                 bool bad = false;
@@ -721,7 +732,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_batch(BatchArgs a) {
             const uint32_t src = I.src;
             uint32_t *dist = reinterpret_cast<uint32_t *>(I.dist);
             for (uint32_t v = team_thread(); v < t.n; v += team_threads()) {
-                const unsigned long long p = __ldcg(t.packed + v);
+                const unsigned long long p = __ldcg(t.pk(v));
                 const uint32_t key = (uint32_t)(p >> 32), low = (uint32_t)p;
                 const bool reached = key < inf_key<DT>();
                 uint32_t pr = NONE, tree = NONE;
@@ -787,7 +798,10 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
     const uint32_t tid = threadIdx.x;
     const uint32_t tt = team_thread(), nt = team_threads();
     const size_t off = (size_t)(blockIdx.x / cl.num_blocks()) * a.cap;
-    double *acc = reinterpret_cast<double *>(a.ws.packed + off);     // subtree sums
+    // subtree sums in the packed words (stride pst: the stamps beside them in a
+    // record are kept for the next forward run)
+    double *acc = reinterpret_cast<double *>(a.ws.packed + off * a.ws.pst);
+    const uint32_t ast = a.ws.pst;
     uint32_t *L[2] = {reinterpret_cast<uint32_t *>(a.ws.F0 + off), reinterpret_cast<uint32_t *>(a.ws.F0 + off) + a.cap};
     uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws.F1 + off);     // children not yet summed
     for (;;) {
@@ -800,7 +814,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
         const uint32_t n = a.graphs[I.graph].n, m = a.graphs[I.graph].m;
         const float *c = a.c[I.orig];
         double *g64 = a.grad64[I.graph];
-        for (uint32_t v = tt; v < n; v += nt) { acc[v] = 0.0; cnt[v] = 0u; }
+        for (uint32_t v = tt; v < n; v += nt) { acc[(size_t)v * ast] = 0.0; cnt[v] = 0u; }
         if (leader && tid == 0) { bs.n[0] = bs.n[1] = 0u; bs.reached = 0u; bs.done = 0u; }
         cl.sync();
         uint32_t reached = 0;
@@ -822,13 +836,13 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
             if (cnt_cur == 0u) break;
             for (uint32_t k = tt; k < cnt_cur; k += nt) {
                 const uint32_t v = __ldcg(L[cur] + k);
-                const double sum = __ldcg(acc + v) + (double)c[v];
+                const double sum = __ldcg(acc + (size_t)v * ast) + (double)c[v];
                 ++done;
                 if (v == I.src) continue;
                 const uint32_t e = I.tree[v], p = I.parent[v];
                 if (e < m) atomicAdd(g64 + e, sum);
                 if (p < n) {
-                    atomicAdd(acc + p, sum);
+                    atomicAdd(acc + (size_t)p * ast, sum);
                     if (atomicSub(cnt + p, 1u) == 1u) L[cur ^ 1u][atomicAdd(&Ls->n[cur ^ 1u], 1u)] = p;
                 }
             }
@@ -906,6 +920,8 @@ cudaError_t team_solve_launch(dsssp_graph *g, const Split *sp, int32_t src, doub
     a.ws.nstamp = w.near_stamp;
     a.ws.sstamp = w.s_stamp;
     a.ws.fflag = w.b_stamp;
+    a.ws.pst = 1u;
+    a.ws.sts = 1u;
     a.ws.F0 = w.F0;
     a.ws.F1 = w.F1;
     a.ws.S0 = w.S0;
@@ -1227,9 +1243,12 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
             w += up256(each * cap * teams);
             return p;
         };
-        b->ws.packed = (unsigned long long *)take(8);
-        b->ws.nstamp = (uint32_t *)take(4);
-        b->ws.sstamp = (uint32_t *)take(4);
+        char *rec = take(16);          // (packed, nstamp, sstamp) per vertex
+        b->ws.packed = (unsigned long long *)rec;
+        b->ws.nstamp = (uint32_t *)rec + 2;
+        b->ws.sstamp = (uint32_t *)rec + 3;
+        b->ws.pst = 2u;
+        b->ws.sts = 4u;
         b->ws.fflag = (uint32_t *)take(4);
         b->ws.F0 = (uint2 *)take(8);
         b->ws.F1 = (uint2 *)take(8);
@@ -1294,8 +1313,7 @@ dsssp_status dsssp_batch_create(dsssp_graph *const *graphs, int32_t n_graphs, co
     if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_m_of, b->m_of.data(), sizeof(uint32_t) * n_graphs, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_stats, 0, sizeof(long long) * kBStats * n_inst, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.nstamp, 0, 4 * cap * teams, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.sstamp, 0, 4 * cap * teams, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.packed, 0, 16 * cap * teams, st);   // records: stamps 0
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.fflag, 0, 4 * cap * teams, st);
     if (tape) {
         if (e == cudaSuccess)

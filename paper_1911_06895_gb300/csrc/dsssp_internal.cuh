@@ -2,6 +2,7 @@
 // kernels (split, solve) and its host API. Not part of the public ABI.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -113,6 +114,10 @@ enum Mode : uint32_t {
 // lower edge) and skipped. Distances beyond the window go to the overflow list,
 // which is redistributed into a new window when the current one is used up.
 constexpr uint32_t kSlots = 32;
+// Merge-path directories of the single-source solver's arc lists: F0, F1, S0,
+// S1, then one per bucket slot.
+constexpr uint32_t kDirSL = 4;
+constexpr uint32_t kDirLists = kDirSL + kSlots;
 
 // Arc lists (frontier F, set S, slot lists) hold uint2 entries (vertex, exclusive
 // arc offset of the entry within its list). An entry is appended with one
@@ -158,8 +163,9 @@ struct alignas(16) SerialState {
     uint64_t t_start;
     uint32_t wepoch;        // window epoch (refills of the slot window)
     uint32_t pad0;
-    long long st[16];
+    long long st[16];       // counters (StatIdx), only ever added to during a solve
 };
+constexpr int kSerialHotVec = (int)(offsetof(SerialState, st) / 16);   // 16-byte words before st[]
 
 // The published view of the next phase: kViewWords 64-bit words, each the
 // phase number (high half) and one 32-bit field (low half). A word is written
@@ -213,6 +219,7 @@ struct SolveArgs {
     uint2 *SL;                      // kSlots x n
     uint32_t *SH;                   // kSlots x n
     uint32_t *OV0, *OV1;            // n each
+    uint2 *dir;                     // kDirLists x dcap: merge-path directory of each arc list
     Ctl *ctl;
     double delta;
     int64_t timeout_ns;
@@ -226,6 +233,7 @@ struct SolveArgs {
     int32_t dtype;
     int32_t test_hook;
     uint32_t nblocks;
+    uint32_t dcap;                  // directory entries per list
 };
 
 // Launch helpers implemented in solve.cu / split.cu (host side).
@@ -238,6 +246,7 @@ cudaError_t launch_split(int64_t n, int64_t m, const uint32_t *off, const int32_
 size_t split_scratch_tiles(int64_t m);
 
 cudaError_t launch_init(const SolveArgs &a, cudaStream_t st);
+uint32_t solve_dir_entries(uint32_t n, uint32_t m);   // directory entries per list
 cudaError_t launch_solve_persistent(const SolveArgs &a, int grid, int block, cudaStream_t st);
 cudaError_t solve_occupancy(int block, int *blocks_per_sm);
 cudaError_t launch_phase_stepped(const SolveArgs &a, uint32_t mode, int grid, int block,

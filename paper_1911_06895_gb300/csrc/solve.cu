@@ -60,11 +60,14 @@ constexpr int kMaxWarps = 16;          // blocks of at most 512 threads
 #endif
 
 constexpr int kIlp = DSSSP_ILP;        // independent 32-arc steps per warp iteration
-constexpr uint32_t kMinSlice = 32u;    // merge-path units of the smallest slice a warp takes
+constexpr uint32_t kMinSlice = 64u;    // merge-path units of the smallest slice a warp takes
 #ifndef DSSSP_ENTRY_COST
 #define DSSSP_ENTRY_COST 4
 #endif
 constexpr uint32_t kEntryCost = DSSSP_ENTRY_COST;   // arcs' worth of work per list entry (merge-path weight)
+// Merge-path directory: a warp's slice starts and ends on a multiple of kDirChunk
+// units, whose positions in the list are recorded when entries are appended.
+constexpr uint32_t kDirChunk = kMinSlice;
 constexpr uint32_t kNoSlot = kSlots;
 
 template <typename T>
@@ -132,10 +135,13 @@ __device__ __forceinline__ void flush_slot_entries32(const SolveArgs &a, const u
         else old = atomicAdd(&c->ctrSL[slot], ((unsigned long long)__popc(grp) << 32) | tot);
     }
     old = __shfl_sync(FULL, old, __ffs(grp) - 1);
+    const bool light = has && (key & 1u) == 0u;
+    const uint32_t idx = (uint32_t)(old >> 32) + rank, off = (uint32_t)old + excl;
     if (has) {
         if (key & 1u) a.SH[(size_t)slot * a.n + (uint32_t)old + rank] = v;
-        else a.SL[(size_t)slot * a.n + (uint32_t)(old >> 32) + rank] = make_uint2(v, (uint32_t)old + excl);
+        else a.SL[(size_t)slot * a.n + idx] = make_uint2(v, off);
     }
+    wu::dir_record<kEntryCost, kDirChunk>(a.dir + (size_t)(kDirSL + slot) * a.dcap, light, idx, off, d);
 }
 
 __device__ __forceinline__ void flush_slot_entries(const SolveArgs &a, const uint32_t *bt, const uint32_t *bv,
@@ -167,6 +173,13 @@ __device__ __forceinline__ unsigned long long *ctr_F(const SolveArgs &a, const P
     return &a.ctl->ctrF[d.cur ^ 1u];
 }
 __device__ __forceinline__ uint2 *dst_S(const SolveArgs &a, const PhaseDesc &d) { return d.spush ? a.S1 : a.S0; }
+// directories of the lists written (F0, F1, S0, S1, then the slot lists)
+__device__ __forceinline__ uint2 *dir_F(const SolveArgs &a, const PhaseDesc &d) {
+    return a.dir + (size_t)(d.cur ? 0u : 1u) * a.dcap;
+}
+__device__ __forceinline__ uint2 *dir_S(const SolveArgs &a, const PhaseDesc &d) {
+    return a.dir + (size_t)(d.spush ? 3u : 2u) * a.dcap;
+}
 __device__ __forceinline__ unsigned long long *ctr_S(const SolveArgs &a, const PhaseDesc &d) {
     return &a.ctl->ctrS[d.spush];
 }
@@ -201,8 +214,8 @@ __device__ __forceinline__ void stage_slot_entry(const SolveArgs &a, bool pred, 
 __device__ __forceinline__ void stage_pushes(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws,
                                              const Push &p, uint32_t v) {
     if (__ballot_sync(FULL, p.f || p.s || p.b || p.ov) == 0u) return;
-    stage_arc_entry(p.f, v, p.fdeg, ws.fv, ws.fd, q.nf, dst_F(a, d), ctr_F(a, d));
-    stage_arc_entry(p.s, v, p.sdeg, ws.sv, ws.sd, q.ns, dst_S(a, d), ctr_S(a, d));
+    stage_arc_entry<kEntryCost, kDirChunk>(p.f, v, p.fdeg, ws.fv, ws.fd, q.nf, dst_F(a, d), ctr_F(a, d), dir_F(a, d));
+    stage_arc_entry<kEntryCost, kDirChunk>(p.s, v, p.sdeg, ws.sv, ws.sd, q.ns, dst_S(a, d), ctr_S(a, d), dir_S(a, d));
     stage_slot_entry(a, p.b, p.slot, v, p.bdeg, ws, q.nb);
     const uint32_t oi = ov_index(d);
     stage_id(p.ov, v, ws.ov, q.nov, oi ? a.OV1 : a.OV0, &a.ctl->nOV[oi]);
@@ -210,8 +223,8 @@ __device__ __forceinline__ void stage_pushes(const SolveArgs &a, const PhaseDesc
 
 // Flush the partially filled staging buffers (end of a phase).
 __device__ __forceinline__ void drain_pushes(const SolveArgs &a, const PhaseDesc &d, PushCnt &q, WarpStage &ws) {
-    if (q.nf) flush_arc_entries(ws.fv, ws.fd, q.nf, dst_F(a, d), ctr_F(a, d));
-    if (q.ns) flush_arc_entries(ws.sv, ws.sd, q.ns, dst_S(a, d), ctr_S(a, d));
+    if (q.nf) flush_arc_entries<kEntryCost, kDirChunk>(ws.fv, ws.fd, q.nf, dst_F(a, d), ctr_F(a, d), dir_F(a, d));
+    if (q.ns) flush_arc_entries<kEntryCost, kDirChunk>(ws.sv, ws.sd, q.ns, dst_S(a, d), ctr_S(a, d), dir_S(a, d));
     if (q.nb) flush_slot_entries(a, ws.bt, ws.bv, ws.bd, q.nb);
     if (q.nov) {
         const uint32_t oi = ov_index(d);
@@ -363,47 +376,24 @@ __device__ void phase_arcs(const SolveArgs &a, const BlockView &bvw, BlockAcc &a
     // Merge-path over the list's entries and arcs together: an entry costs
     // kEntryCost arcs' worth of work (its share of a window load and of the owner
     // mapping), so a slice of many short segments gets fewer arcs. In merged
-    // order the first arc of entry i sits at (i + 1) * kEntryCost + offs[i]; at
-    // least kMinSlice units per warp (small phases use few warps).
+    // order the first arc of entry i sits at (i + 1) * kEntryCost + offs[i]. A
+    // warp's slice is a run of kDirChunk-unit chunks (small phases use few
+    // warps); where a chunk boundary falls in the list was recorded in the list's
+    // directory when the entries were appended, so no search is needed.
+    const uint2 *dir = a.dir + (size_t)(LIGHT ? (from_slot ? kDirSL + sl : (d.cur ? 1u : 0u)) : (d.scur ? 3u : 2u)) * a.dcap;
     const unsigned long long W = (unsigned long long)count * kEntryCost + E;
-    const unsigned long long want_w = (W + kMinSlice - 1u) / kMinSlice;
-    const uint32_t nw = want_w < (unsigned long long)nw_all ? (uint32_t)want_w : nw_all;
+    const uint32_t nch = (uint32_t)((W + kDirChunk - 1u) / kDirChunk);
+    const uint32_t nw = nch < nw_all ? nch : nw_all;
     if (gw < nw) {
-        const unsigned long long d0 = W * gw / nw, d1 = W * (gw + 1) / nw;
-        // i0 / i1 = number of entries whose first arc lies at or before d0 / d1:
-        // two 32-ary searches in step, down to fewer than 32 candidates each
-        uint32_t lo0 = 0, hi0 = count, lo1 = 0, hi1 = count;
-        while (hi0 - lo0 > 31u || hi1 - lo1 > 31u) {
-            const uint32_t st0 = (hi0 - lo0 + 31u) >> 5, st1 = (hi1 - lo1 + 31u) >> 5;
-            const uint32_t p0 = lo0 + lane * st0, p1 = lo1 + lane * st1;
-            const bool ok0 = hi0 - lo0 > 31u && p0 < hi0 &&
-                             (unsigned long long)(p0 + 1u) * kEntryCost + __ldcg(offs + 2ull * p0) <= d0;
-            const bool ok1 = hi1 - lo1 > 31u && p1 < hi1 &&
-                             (unsigned long long)(p1 + 1u) * kEntryCost + __ldcg(offs + 2ull * p1) <= d1;
-            const uint32_t k0 = __popc(__ballot_sync(FULL, ok0)), k1 = __popc(__ballot_sync(FULL, ok1));
-            if (hi0 - lo0 > 31u) {
-                hi0 = min(hi0, lo0 + k0 * st0);
-                lo0 = k0 ? lo0 + (k0 - 1u) * st0 + 1u : lo0;
-            }
-            if (hi1 - lo1 > 31u) {
-                hi1 = min(hi1, lo1 + k1 * st1);
-                lo1 = k1 ? lo1 + (k1 - 1u) * st1 + 1u : lo1;
-            }
-        }
-        // final round: lane j probes lo + j (up to hi inclusive) and keeps its offset
-        uint32_t i0, i1, o0, o1;
-        {
-            const uint32_t p0 = lo0 + lane, p1 = lo1 + lane;
-            const uint32_t v0 = p0 <= hi0 ? (p0 < count ? __ldcg(offs + 2ull * p0) : E) : E;
-            const uint32_t v1 = p1 <= hi1 ? (p1 < count ? __ldcg(offs + 2ull * p1) : E) : E;
-            const bool ok0 = p0 < hi0 && (unsigned long long)(p0 + 1u) * kEntryCost + v0 <= d0;
-            const bool ok1 = p1 < hi1 && (unsigned long long)(p1 + 1u) * kEntryCost + v1 <= d1;
-            const uint32_t k0 = __popc(__ballot_sync(FULL, ok0)), k1 = __popc(__ballot_sync(FULL, ok1));
-            i0 = lo0 + k0;
-            i1 = lo1 + k1;
-            o0 = __shfl_sync(FULL, v0, k0);          // offset of entry i0 (E when i0 == count)
-            o1 = __shfl_sync(FULL, v1, k1);
-        }
+        const uint32_t c0 = (uint32_t)((unsigned long long)nch * gw / nw);
+        const uint32_t c1 = (uint32_t)((unsigned long long)nch * (gw + 1u) / nw);
+        const unsigned long long d0 = (unsigned long long)c0 * kDirChunk;
+        const unsigned long long d1 = c1 < nch ? (unsigned long long)c1 * kDirChunk : W;
+        // (i, o) = number of entries whose first arc lies at or before the
+        // boundary, and the arc offset of the entry after them (E past the last)
+        const uint2 p0 = c0 != 0u ? __ldcg(dir + c0) : make_uint2(0u, 0u);
+        const uint2 p1 = c1 < nch ? __ldcg(dir + c1) : make_uint2(count, E);
+        const uint32_t i0 = p0.x, o0 = p0.y, i1 = p1.x, o1 = p1.y;
         const uint32_t e0 = (uint32_t)min(d0 - (unsigned long long)i0 * kEntryCost, (unsigned long long)o0);
         const uint32_t e1 = (uint32_t)min(d1 - (unsigned long long)i1 * kEntryCost, (unsigned long long)o1);
         // the entry owning arc e0
@@ -699,13 +689,19 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
     Ctl *c = a.ctl;
     const uint32_t lane = lane_id();
     const bool l0 = lane == 0u;
+    // the control part of the serial state goes through registers; the
+    // counters of st[] are only added to (lane 0, atomics whose result is unused)
     SerialState s;
     {
         const uint4 *src = reinterpret_cast<const uint4 *>(&c->ss);
         uint4 *dst = reinterpret_cast<uint4 *>(&s);
         #pragma unroll
-        for (int k = 0; k < (int)(sizeof(SerialState) / 16); ++k) dst[k] = __ldcg(src + k);
+        for (int k = 0; k < kSerialHotVec; ++k) dst[k] = __ldcg(src + k);
     }
+    long long *st = c->ss.st;
+    auto stat = [&](int k, long long v) {
+        if (l0) atomicAdd(reinterpret_cast<unsigned long long *>(st + k), (unsigned long long)v);
+    };
     PhaseDesc od;                                  // the phase that just ended
     #pragma unroll
     for (int k = 0; k < kDescVec; ++k)
@@ -737,14 +733,14 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
 
     const uint64_t dt = now - s.t_last;
     if (t_first > s.t_last && t_first <= now) {      // persistent mode only
-        s.st[ST_NSFIRST] += (long long)(t_first - s.t_last);
-        s.st[ST_NSSPREAD] += (long long)(now - t_first);
+        stat(ST_NSFIRST, (long long)(t_first - s.t_last));
+        stat(ST_NSSPREAD, (long long)(now - t_first));
     }
     s.t_last = now;
     const uint32_t mode = s.mode;
-    if (mode == MODE_LIGHT) s.st[ST_NSLIGHT] += (long long)dt;
-    else if (mode == MODE_HEAVY || mode == MODE_FUSED) s.st[ST_NSHEAVY] += (long long)dt;
-    else if (mode == MODE_REBIN) s.st[ST_NSREBIN] += (long long)dt;
+    if (mode == MODE_LIGHT) stat(ST_NSLIGHT, (long long)dt);
+    else if (mode == MODE_HEAVY || mode == MODE_FUSED) stat(ST_NSHEAVY, (long long)dt);
+    else if (mode == MODE_REBIN) stat(ST_NSREBIN, (long long)dt);
     s.phases += 1;
     PhaseDesc nd{};
     nd.slot = kNoSlot;
@@ -759,32 +755,32 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
     } else {
         switch (mode) {
         case MODE_LIGHT:
-            s.st[ST_LIGHT] += 1;
+            stat(ST_LIGHT, 1);
             if (od.slot < kNoSlot) {               // the bucket's slot is consumed
-                s.st[ST_VLIGHT] += (long long)od.count;
+                stat(ST_VLIGHT, (long long)od.count);
                 if (l0) {
                     c->ctrSL[od.slot] = 0ull;
                     c->nSH[od.slot] = 0u;
                 }
             } else {
-                s.st[ST_VLIGHT] += (long long)(ctrF[s.cur] >> 32);
+                stat(ST_VLIGHT, (long long)(ctrF[s.cur] >> 32));
                 if (l0) c->ctrF[s.cur] = 0ull;
                 ctrF[s.cur] = 0ull;
             }
             break;
         case MODE_HEAVY:
-            s.st[ST_HEAVY] += 1;
-            s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
+            stat(ST_HEAVY, 1);
+            stat(ST_VHEAVY, (long long)(ctrS[s.scur] >> 32));
             if (l0) c->ctrS[s.scur] = 0ull;
             ctrS[s.scur] = 0ull;
             s.scur ^= 1u;               // S pushed during the heavy pass (a re-opened bucket)
             s.sround += 1u;
             break;
         case MODE_FUSED:                           // bucket i's S and bucket i+1's slot are consumed
-            s.st[ST_LIGHT] += 1;
-            s.st[ST_HEAVY] += 1;
-            s.st[ST_VLIGHT] += (long long)od.count;
-            s.st[ST_VHEAVY] += (long long)(ctrS[s.scur] >> 32);
+            stat(ST_LIGHT, 1);
+            stat(ST_HEAVY, 1);
+            stat(ST_VLIGHT, (long long)od.count);
+            stat(ST_VHEAVY, (long long)(ctrS[s.scur] >> 32));
             if (l0) {
                 c->ctrSL[od.slot] = 0ull;
                 c->nSH[od.slot] = 0u;
@@ -795,7 +791,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
             s.sround += 1u;
             break;
         case MODE_REBIN:
-            s.st[ST_REBIN] += 1;
+            stat(ST_REBIN, 1);
             if (l0) c->nOV[s.ov_cur] = 0u;
             s.ov_cur ^= 1u;
             break;
@@ -821,7 +817,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
             if (a.fuse && first >= 0 && found == first) {
                 next_mode = MODE_FUSED;
                 s.bucket += 1;
-                s.st[ST_BUCKETS] += 1;
+                stat(ST_BUCKETS, 1);
                 s.T_lo = flo;
                 s.T = fhi;
                 nd.slot = (uint32_t)found;
@@ -837,7 +833,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
             }
         } else if (found >= 0) {                   // next non-empty bucket of the window
             s.bucket = s.wbase + found;
-            s.st[ST_BUCKETS] += 1;
+            stat(ST_BUCKETS, 1);
             s.T_lo = flo;
             s.T = fhi;
             next_mode = MODE_LIGHT;
@@ -874,7 +870,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
             nd.count = nov[s.ov_cur];
         }
     }
-    if (next_mode == MODE_DONE) s.st[ST_NSTOTAL] = (long long)(now - s.t_start);
+    if (next_mode == MODE_DONE && l0) st[ST_NSTOTAL] = (long long)(now - s.t_start);
     s.mode = next_mode;
     nd.mode = next_mode;
     nd.cur = s.cur;
@@ -896,7 +892,7 @@ __device__ __noinline__ void serial_step(const SolveArgs &a, BlockView *out) {
         const uint4 *src = reinterpret_cast<const uint4 *>(&s);
         uint4 *dst = reinterpret_cast<uint4 *>(&c->ss);
         #pragma unroll
-        for (int k = 0; k < (int)(sizeof(SerialState) / 16); ++k) dst[k] = src[k];
+        for (int k = 0; k < kSerialHotVec; ++k) dst[k] = src[k];
         const uint4 *ds = reinterpret_cast<const uint4 *>(&nd);
         uint4 *dd = reinterpret_cast<uint4 *>(&c->desc);
         #pragma unroll
@@ -1126,6 +1122,19 @@ __global__ void k_init(SolveArgs a) {
         a.b_stamp[v] = 0u;
         a.ov_flag[v] = 0u;
     }
+    {
+        // directories of F0 and S0, which hold the source's entry (0, offset 0):
+        // boundary 0 lies in the entry's own units, every later one in its arcs
+        const uint4 vs = a.vinfo[a.src];
+        const uint32_t dl = vs.y - vs.x, dh = vs.z - vs.y;
+        const uint32_t nl = dl ? (uint32_t)(((unsigned long long)kEntryCost + dl + kDirChunk - 1u) / kDirChunk) : 0u;
+        const uint32_t nh = dh ? (uint32_t)(((unsigned long long)kEntryCost + dh + kDirChunk - 1u) / kDirChunk) : 0u;
+        uint2 *dF = a.dir, *dS = a.dir + 2ull * a.dcap;
+        for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nl; c += gridDim.x * blockDim.x)
+            dF[c] = c ? make_uint2(1u, dl) : make_uint2(0u, 0u);
+        for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nh; c += gridDim.x * blockDim.x)
+            dS[c] = c ? make_uint2(1u, dh) : make_uint2(0u, 0u);
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         Ctl *c = a.ctl;
         const uint4 vs = a.vinfo[a.src];
@@ -1193,6 +1202,10 @@ cudaError_t launch_init(const SolveArgs &a, cudaStream_t st) {
     if (a.dtype == DSSSP_F32) k_init<DSSSP_F32><<<grid_for(a.n, 256), 256, 0, st>>>(a);
     else k_init<DSSSP_I32><<<grid_for(a.n, 256), 256, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+uint32_t solve_dir_entries(uint32_t n, uint32_t m) {
+    return (uint32_t)(((unsigned long long)n * kEntryCost + m) / kDirChunk + 2u);
 }
 
 size_t stage_bytes(int block) { return (size_t)(block / 32) * sizeof(WarpStage); }
