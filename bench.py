@@ -58,8 +58,8 @@ B_VERTEX, B_ARC, B_FAR, B_INIT_UNPACK = 28, 16, 20, 36
 # DRAM traffic of k_solve_persistent per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum), mean of
 # one launch at each Delta of the sweep, from one ncu capture of the profiling driver below. It holds only
 # for the kernel source the counters were taken on; any other source reports null.
-TRAFFIC_BYTES_PER_LAUNCH = 3.113e9
-TRAFFIC_SOURCE_SHA256 = "4557af3d8999a5ee83478d66ba418250862ae21d9c37bbffd556999601f42b82"
+TRAFFIC_BYTES_PER_LAUNCH = 3.124e9
+TRAFFIC_SOURCE_SHA256 = "991d94bdf0a8ee8566320598760666b48cb686a68a355e4681e27ac2bc674a19"
 
 
 def measured_traffic(scale: int):
