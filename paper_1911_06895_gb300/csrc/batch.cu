@@ -798,10 +798,9 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
     const uint32_t tid = threadIdx.x;
     const uint32_t tt = team_thread(), nt = team_threads();
     const size_t off = (size_t)(blockIdx.x / cl.num_blocks()) * a.cap;
-    // subtree sums in the packed words (stride pst: the stamps beside them in a
-    // record are kept for the next forward run)
-    double *acc = reinterpret_cast<double *>(a.ws.packed + off * a.ws.pst);
-    const uint32_t ast = a.ws.pst;
+    // subtree sums in the S0 list's memory (8 bytes per vertex, contiguous; the
+    // records' stamps are kept for the next forward run)
+    double *acc = reinterpret_cast<double *>(a.ws.S0 + off);
     uint32_t *L[2] = {reinterpret_cast<uint32_t *>(a.ws.F0 + off), reinterpret_cast<uint32_t *>(a.ws.F0 + off) + a.cap};
     uint32_t *cnt = reinterpret_cast<uint32_t *>(a.ws.F1 + off);     // children not yet summed
     for (;;) {
@@ -814,7 +813,7 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
         const uint32_t n = a.graphs[I.graph].n, m = a.graphs[I.graph].m;
         const float *c = a.c[I.orig];
         double *g64 = a.grad64[I.graph];
-        for (uint32_t v = tt; v < n; v += nt) { acc[(size_t)v * ast] = 0.0; cnt[v] = 0u; }
+        for (uint32_t v = tt; v < n; v += nt) { acc[v] = 0.0; cnt[v] = 0u; }
         if (leader && tid == 0) { bs.n[0] = bs.n[1] = 0u; bs.reached = 0u; bs.done = 0u; }
         cl.sync();
         uint32_t reached = 0;
@@ -836,13 +835,13 @@ __global__ void __launch_bounds__(kTeamThreads, 2) k_backward(BwdArgs a) {
             if (cnt_cur == 0u) break;
             for (uint32_t k = tt; k < cnt_cur; k += nt) {
                 const uint32_t v = __ldcg(L[cur] + k);
-                const double sum = __ldcg(acc + (size_t)v * ast) + (double)c[v];
+                const double sum = __ldcg(acc + v) + (double)c[v];
                 ++done;
                 if (v == I.src) continue;
                 const uint32_t e = I.tree[v], p = I.parent[v];
                 if (e < m) atomicAdd(g64 + e, sum);
                 if (p < n) {
-                    atomicAdd(acc + (size_t)p * ast, sum);
+                    atomicAdd(acc + p, sum);
                     if (atomicSub(cnt + p, 1u) == 1u) L[cur ^ 1u][atomicAdd(&Ls->n[cur ^ 1u], 1u)] = p;
                 }
             }
