@@ -375,8 +375,12 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
                 }
             }
             uint2 arc[kTIlp];
+            uint32_t pin[kTIlp];       // tape: the arc's input index, loaded beside the arc (same positions)
             #pragma unroll
-            for (int k = 0; k < kTIlp; ++k) arc[k] = ok[k] ? __ldcs(t.arcs + ai[k]) : make_uint2(0u, 0u);
+            for (int k = 0; k < kTIlp; ++k) {
+                arc[k] = ok[k] ? __ldcs(t.arcs + ai[k]) : make_uint2(0u, 0u);
+                if (TAPE) pin[k] = ok[k] ? __ldcs(t.perm + ai[k]) : NONE;
+            }
             uint32_t ck[kTIlp];
             unsigned long long cur[kTIlp], cand[kTIlp];
             #pragma unroll
@@ -385,14 +389,9 @@ __device__ void team_relax(const Team &t, const Ph &ph, TStage &ws, int *sl, uin
                 ovf |= ok[k] && ck[k] >= inf_key<DT>();
                 cur[k] = ck[k] < inf_key<DT>() ? __ldcg(t.pk(arc[k].x)) : 0ull;
             }
-            // with a tape the low word is the arc's input index, read only for a
-            // request that can win or tie on the key
+            // with a tape the low word is the arc's input index
             #pragma unroll
-            for (int k = 0; k < kTIlp; ++k) {
-                uint32_t low = ov[k];
-                if (TAPE) low = (ck[k] < inf_key<DT>() && ck[k] <= (uint32_t)(cur[k] >> 32)) ? __ldcs(t.perm + ai[k]) : NONE;
-                cand[k] = ((unsigned long long)ck[k] << 32) | low;
-            }
+            for (int k = 0; k < kTIlp; ++k) cand[k] = ((unsigned long long)ck[k] << 32) | (TAPE ? pin[k] : ov[k]);
             // packed[v] only decreases: a value read earlier bounds it, so the
             // atomic is skipped when the request cannot win (old = 0: no win)
             unsigned long long old[kTIlp];
